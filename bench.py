@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of the sliding-window-analysis hot path on GB300.
+
+One step = one pass of the whole path over one image: build S and Q
+(swa_build_sat), evaluate every window size of the workload on them
+(swa_window_stats_multi) and release the tables (swa_free).
+
+Default workload: the 70,000 x 85,000 uint8 synthetic microscopy image
+(5.95e9 px, 95 GB of tables) with windows 256 and 1024 at stride 16.
+``--workload 1`` runs the 20,000 x 20,000 image with windows 50/100/200 at
+stride 1.
+
+Prints one JSON line.  ``value`` is image pixels per second of the whole step
+(Gpx/s) with the image resident in HBM; ``e2e`` is the same metric through
+``swa_analyze`` with the image in pinned host memory and the results copied
+back to host memory inside the timed region.  ``--impl reference`` times the
+CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SAT build Gpx/s + window outputs/s, % HBM peak; served p50/p99 vs plain path"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=0,
+                    help="rows of the CPU-baseline sample (0: sized to ~10 s)")
+    ap.add_argument("--twopass", action="store_true", help="force the two-pass SAT build")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers --
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def gpu_id_for_smi(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return local_rank
+
+
+def distinct_corner_bytes(rows, cols, wh, ww, sy, sx, tables):
+    """Bytes of the distinct table entries a window query reads: rows
+    {i*sy - 1, i*sy + wh - 1} x columns {j*sx - 1, j*sx + ww - 1} (index -1
+    excluded), 8 bytes per entry per table."""
+    R = (rows - wh) // sy + 1
+    C = (cols - ww) // sx + 1
+    i = np.arange(R, dtype=np.int64)
+    j = np.arange(C, dtype=np.int64)
+    ry = np.unique(np.concatenate([i * sy - 1, i * sy + wh - 1]))
+    cx = np.unique(np.concatenate([j * sx - 1, j * sx + ww - 1]))
+    return int((ry >= 0).sum()) * int((cx >= 0).sum()) * 8 * tables
+
+
+def traffic_record(kernel):
+    """ncu DRAM bytes per launch for `kernel`, if the committed capture is of
+    the current source; else None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    import hashlib
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2410_16291_gb300", "csrc", e["source"])
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != e["source_sha"]:
+        return None
+    return e["bytes_per_launch_full"]
+
+
+# --------------------------------------------------------------- CPU legs --
+
+def oracle_sample(img_rows_fn, cols, windows, rows):
+    """Time the CPU oracle on the first `rows` full-width rows of the image:
+    tables, then every window of the workload that fits."""
+    import oracle
+    sample = img_rows_fn(rows)
+    t0 = time.perf_counter()
+    S, Q = oracle.sat(sample)
+    outs = 0
+    for (wh, ww, sy, sx) in windows:
+        if wh <= rows:
+            r = oracle.window_sat(S, Q, wh, ww, sy, sx)
+            outs += r["sum"].size
+    dt = time.perf_counter() - t0
+    return sample.size, outs, dt
+
+
+def cpu_baseline(im, windows, rows):
+    import synth
+
+    def rows_fn(n):
+        return synth.intensity_u8(n, im.cols, im.seed, synth.cluster_count(n, im.cols))
+    if rows <= 0:
+        px, _, dt = oracle_sample(rows_fn, im.cols, windows, 256)
+        rows = int(256 * min(20.0, 12.0 / max(dt, 1e-3)))
+        rows = max(1024, min(rows, im.rows, 16384))
+        try:
+            import psutil
+            free = psutil.virtual_memory().available
+            rows = max(1024, min(rows, int(free * 0.4 / (17 * im.cols))))
+        except ImportError:
+            pass
+    px, outs, dt = oracle_sample(rows_fn, im.cols, windows, rows)
+    return {"value": px / dt / 1e9, "unit": "Gpx/s", "cores": 1, "kind": "oracle",
+            "sample": "%d x %d rows of the workload's generator (%.2e px), tables + the "
+                      "workload's windows that fit, serial C, %.1f s" % (rows, im.cols, px, dt)}
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores as the reference arm: each step is a
+    bounded sample (1024 full-width rows) of the workload."""
+    import synth
+    if rank != 0:
+        return
+    (im,) = synth.workload(args.workload)
+    windows = [(w.wh, w.ww, w.sy, w.sx) for w in im.windows]
+    rows = max(w[0] for w in windows)
+    rows = max(rows, 1024)
+
+    def rows_fn(n):
+        return synth.intensity_u8(n, im.cols, im.seed, synth.cluster_count(n, im.cols))
+    for _ in range(args.warmup):
+        oracle_sample(rows_fn, im.cols, windows, rows)
+    tot_px, tot_out, tot_t = 0, 0, 0.0
+    for _ in range(args.steps):
+        px, outs, dt = oracle_sample(rows_fn, im.cols, windows, rows)
+        tot_px += px
+        tot_out += outs
+        tot_t += dt
+    v = tot_px / tot_t / 1e9
+    line = {"metric": METRIC, "value": v, "unit": "Gpx/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "impl": "reference",
+            "config": config_of(im, windows),
+            "window_outputs_per_s": tot_out / tot_t,
+            "cpu_baseline": {"value": v, "unit": "Gpx/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d x %d rows per step, serial C oracle" % (rows, im.cols)},
+            "e2e": {"value": v, "unit": "Gpx/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(im, windows):
+    return {"workload": "%dx%d %s synthetic microscopy image, %d clusters" % (
+        im.rows, im.cols, im.dtype, im.n_clusters),
+        "windows": ["%dx%d/s%d" % (w[0], w[1], w[2]) for w in windows],
+        "outputs": "sum,mean,std", "tables": "S and Q, uint64",
+        "l2": "inputs larger than L2 (image %.2f GB, tables %.1f GB)" % (
+            im.pixels / 1e9, 16 * im.pixels / 1e9)}
+
+
+# ---------------------------------------------------------------- GPU legs --
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2410_16291_gb300 as swa
+    import synth
+    from paper_2410_16291_gb300 import build as swa_build
+    swa_build.build()
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+
+    (im,) = synth.workload(args.workload)
+    windows = [(w.wh, w.ww, w.sy, w.sx) for w in im.windows]
+    px = im.pixels
+    host = torch.empty((im.rows, im.cols), dtype=torch.uint8, pin_memory=True)
+    im.generate(out=host.numpy())
+    dev = host.to("cuda", non_blocking=True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    # Outputs, preallocated once.
+    shapes = [swa.window_shape(im.rows, im.cols, *w) for w in windows]
+    outs = [{"sum": torch.empty(s, dtype=torch.int64, device="cuda"),
+             "mean": torch.empty(s, dtype=torch.float64, device="cuda"),
+             "std": torch.empty(s, dtype=torch.float64, device="cuda")} for s in shapes]
+    n_out = sum(R * C for R, C in shapes)
+
+    def step():
+        sat = swa.build_sat(dev, with_sq=True, twopass=args.twopass)
+        sat.window_stats(windows, out=outs)
+        sat.free()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(gpu_id_for_smi(local_rank))
+    if rank == 0:
+        clocks.start()
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    l0 = swa.lib().swa_launch_count()
+    swa.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = swa.profile_end()
+    launches = swa.lib().swa_launch_count() - l0
+    if dist:
+        td.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.stop() if rank == 0 else None
+
+    # Per-kernel averages and the dominant kernel's roofline.
+    hbm, hbm_kind = peaks()
+    tables = 2
+    build_bytes = px * (1 + 8 * tables)
+    kernels = {}
+    for name, (n, tot, mx) in prof.items():
+        kernels[name] = {"launches": n, "avg_ms": tot / n, "share": 0.0}
+    total_ms = sum(tot for (_, tot, _) in prof.values()) or 1.0
+    for name, (n, tot, mx) in prof.items():
+        kernels[name]["share"] = tot / total_ms
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    bytes_per_launch = {"sat_build": build_bytes, "sat_scan": build_bytes,
+                        "sat_reduce": px * 1}
+    win_bytes = sum(distinct_corner_bytes(im.rows, im.cols, *w, tables) + 24 * R * C
+                    for w, (R, C) in zip(windows, shapes))
+    bytes_per_launch["window_stats"] = win_bytes / len(windows)
+    roof = None
+    if dom is not None and dom in bytes_per_launch:
+        avg = kernels[dom]["avg_ms"]
+        ach = bytes_per_launch[dom] / (avg / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_kind": hbm_kind,
+                "algorithmic_bytes_per_launch": bytes_per_launch[dom],
+                "traffic": traffic_record(dom), "avg_ms": avg}
+    build_ms = sum(kernels[k]["avg_ms"] * kernels[k]["launches"] for k in kernels
+                   if k.startswith("sat_")) / args.steps
+    win_ms = sum(kernels[k]["avg_ms"] * kernels[k]["launches"] for k in kernels
+                 if k.startswith("window")) / args.steps
+
+    # End to end through swa_analyze with host buffers.
+    e2e = None
+    if not args.no_e2e:
+        hout = [{"sum": torch.empty(s, dtype=torch.int64, pin_memory=True),
+                 "mean": torch.empty(s, dtype=torch.float64, pin_memory=True),
+                 "std": torch.empty(s, dtype=torch.float64, pin_memory=True)} for s in shapes]
+        for _ in range(max(1, min(args.warmup, 2))):
+            swa.analyze(host, windows, out=hout)
+        torch.cuda.synchronize()
+        if dist:
+            td.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            swa.analyze(host, windows, out=hout)
+        torch.cuda.synchronize()
+        et = (time.perf_counter() - t0) / args.e2e_steps
+        if dist:
+            t = torch.tensor([et], device="cuda")
+            td.all_reduce(t, op=td.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": world * px / et / 1e9, "unit": "Gpx/s",
+               "h2d_bytes_per_step": px, "d2h_bytes_per_step": 24 * n_out,
+               "ms_per_step": et * 1e3, "steps": args.e2e_steps,
+               "api": "swa_analyze (pinned host image in, pinned host results out)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(im, windows, args.cpu_rows)
+
+    if rank != 0:
+        return
+    value = world * px / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "Gpx/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic", "config": config_of(im, windows),
+            "sat_build_gpx_s": px / (build_ms / 1e3) / 1e9 if build_ms else None,
+            "sat_build_ms": build_ms, "window_ms": win_ms,
+            "window_outputs_per_s": world * n_out / (ms / 1e3),
+            "window_outputs_per_step": n_out,
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk, "gpu_launches": launches,
+            "build_path": "twopass" if args.twopass else "default"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

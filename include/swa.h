@@ -1,0 +1,214 @@
+/*
+ * swa.h -- C ABI of the GB300 sliding-window-analysis library (libswa.so).
+ *
+ * The library computes, on one CUDA device, the method of "Accelerating
+ * Biological Spatial Cluster Analysis with the Parallel Integral Image
+ * Technique" (arXiv 2410.16291):
+ *
+ *   1. the summed-area table (integral image) S of an image and the table Q of
+ *      its squared pixels, as exact uint64 inclusive 2-D prefix sums
+ *      (Section II-B: each entry is the sum of all pixels above and to the
+ *      left of its position, the position included);
+ *   2. for every valid window position, the window's sum, mean and population
+ *      standard deviation, by four lookups at the window's corners
+ *      (Section II-B; the 4(r*c) lookup term of Section III-B), for any
+ *      number of window sizes and strides on one resident table pair
+ *      (Section V names this reuse as the paper's future work).
+ *
+ * Conventions shared by every call:
+ *  - Pointers documented as "device" must be CUDA device (or managed) memory
+ *    of the current device.  swa_analyze alone also accepts host memory.
+ *  - swa_stream is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls enqueue work and return without waiting unless stated.
+ *  - Images are row-major, rows x cols pixels of uint8 or uint16, with a row
+ *    pitch in bytes >= cols * pixel size.
+ *  - Tables are row-major uint64, rows x cols, with a leading dimension
+ *    (elements) reported by swa_sat_data; entries past column cols-1 in a row
+ *    are padding with unspecified contents.
+ *  - Window outputs are row-major R x C arrays with a caller-chosen leading
+ *    dimension out_ld >= C, where R = floor((rows - wh)/sy) + 1 and
+ *    C = floor((cols - ww)/sx) + 1; output (i, j) is the window whose top-left
+ *    pixel is (i*sy, j*sx) (valid windows only, Section III-A's
+ *    (r - w + 1)(c - w + 1) positions at stride 1).
+ *  - mean = Sw / n and std = sqrt(n*Qw - Sw^2) / n, n = wh*ww, where Sw and
+ *    Qw are the window's exact sums of pixels and squared pixels and the
+ *    difference n*Qw - Sw^2 is exact (128-bit).  Sums are exact.
+ *  - Every call returns a swa_status and never aborts.  Errors detected on
+ *    the device (a look-back that waited too long) are reported by swa_sync
+ *    and by later calls on the same handle.
+ *  - Distinct handles may be used from different host threads; one handle
+ *    must not be freed while a call on it is in flight on another thread.
+ */
+#ifndef SWA_H
+#define SWA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swa_sat swa_sat;     /* opaque: owns the device tables S and Q */
+typedef void *swa_stream;           /* a cudaStream_t */
+
+typedef enum { SWA_U8 = 1, SWA_U16 = 2 } swa_dtype;
+
+typedef enum {
+    SWA_OK = 0,
+    SWA_EINVAL = 1,     /* bad argument: null pointer, size <= 0, window larger
+                           than the image, std asked of a table built without Q */
+    SWA_EOVERFLOW = 2,  /* a table entry could exceed 2^64 - 1 (see swa_build_sat) */
+    SWA_ENOMEM = 3,     /* device allocation failed or the memory limit is reached */
+    SWA_ECUDA = 4,      /* a CUDA runtime call or launch failed */
+    SWA_ETIMEOUT = 5    /* a kernel waited too long for another block's result */
+} swa_status;
+
+/* Build flags. */
+enum {
+    SWA_WITH_SQ = 1u,   /* also build Q, the table of squared pixels (needed for std) */
+    SWA_TWOPASS = 2u    /* read the image twice (reduce, then scan) instead of the
+                           single pass with decoupled look-back */
+};
+
+/* Window output selection. */
+enum { SWA_OUT_SUM = 1u, SWA_OUT_MEAN = 2u, SWA_OUT_STD = 4u };
+
+/* One window query: size wh x ww, strides sy, sx, the outputs wanted and
+ * where they go (device pointers; those not selected may be NULL). */
+typedef struct {
+    int64_t wh, ww, sy, sx;
+    uint32_t outputs;           /* SWA_OUT_* bits */
+    uint32_t reserved;          /* must be 0 */
+    uint64_t *sum;              /* R x C, leading dimension out_ld */
+    double *mean;
+    double *std;
+    int64_t out_ld;
+} swa_window;
+
+/*
+ * Build S (and Q with SWA_WITH_SQ) of a device image.  Section II-B defines
+ * the table; Section III-B its O(r*c) cost, here split over the whole GPU.
+ *   d_image      device pointer to rows x cols pixels of dtype, read only, in
+ *                stream order; the caller may free it once the stream has
+ *                passed this call.
+ *   pitch_bytes  distance between rows, >= cols * pixel size; for uint16 the
+ *                base address and the pitch must be even (SWA_EINVAL otherwise).
+ *   flags        SWA_WITH_SQ, SWA_TWOPASS.
+ *   stream       the build runs on it; the handle keeps it as its home stream.
+ *   out          receives a new handle that owns S and Q (stream-ordered
+ *                allocations on `stream`); set to NULL on error.
+ * Returns SWA_EOVERFLOW when rows*cols*max_pixel (or rows*cols*max_pixel^2
+ * with SWA_WITH_SQ) is >= 2^64, so that no entry can wrap: for uint8 this
+ * never happens below 2.8e14 px; a uint16 image with Q must have fewer than
+ * 4,295,098,372 px.
+ */
+swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols,
+                         int64_t pitch_bytes, swa_dtype dtype, uint32_t flags,
+                         swa_stream stream, swa_sat **out);
+
+/* Output grid of valid windows (host only, no device work).  SWA_EINVAL when
+ * a size or stride is <= 0 or the window is larger than the image. */
+swa_status swa_window_shape(int64_t rows, int64_t cols, int64_t wh, int64_t ww,
+                            int64_t sy, int64_t sx, int64_t *out_r, int64_t *out_c);
+
+/*
+ * Sum, mean and std of every valid window (wh x ww, strides sy, sx) by four
+ * corner lookups in S (and Q for std): Section II-B's rectangle sum, the
+ * paper's window sum analysis of Section II-A and the integral-image average
+ * and standard deviation it mentions there.  Outputs are device arrays of
+ * R x C with leading dimension out_ld (see the conventions above); SWA_OUT_STD
+ * needs a handle built with SWA_WITH_SQ.  Runs on `stream` after the build.
+ */
+swa_status swa_window_stats(const swa_sat *sat, int64_t wh, int64_t ww,
+                            int64_t sy, int64_t sx, uint32_t outputs,
+                            uint64_t *d_sum, double *d_mean, double *d_std,
+                            int64_t out_ld, swa_stream stream);
+
+/*
+ * Several window queries on one resident table pair in one launch (the
+ * reuse of one integral image across window sizes that Section V names as
+ * future work).  Same semantics as n calls of swa_window_stats; at most
+ * SWA_MAX_WINDOWS per call.
+ */
+#define SWA_MAX_WINDOWS 64
+swa_status swa_window_stats_multi(const swa_sat *sat, const swa_window *windows,
+                                  int32_t n, swa_stream stream);
+
+/* Borrowed device views of S and Q (Q is NULL without SWA_WITH_SQ) and their
+ * leading dimension in elements.  Valid until swa_free; read them only in
+ * stream order after the build. */
+swa_status swa_sat_data(const swa_sat *sat, const uint64_t **d_S,
+                        const uint64_t **d_Q, int64_t *ld);
+
+/* Shape, dtype and flags of a handle. */
+swa_status swa_sat_info(const swa_sat *sat, int64_t *rows, int64_t *cols,
+                        int32_t *dtype, uint32_t *flags);
+
+/* Device bytes a build of this shape holds while the handle lives (tables)
+ * and transiently during the build (scratch).  Host only. */
+swa_status swa_sat_bytes(int64_t rows, int64_t cols, swa_dtype dtype, uint32_t flags,
+                         int64_t *table_bytes, int64_t *scratch_bytes);
+
+/* Wait for the handle's work on its home stream and on every stream a later
+ * call used, then report any error the device recorded (SWA_ETIMEOUT). */
+swa_status swa_sync(const swa_sat *sat);
+
+/* Release S and Q, stream-ordered on the handle's home stream after every
+ * call made on the handle.  NULL is a no-op; a handle that was already freed
+ * is detected by its tag and ignored. */
+void swa_free(swa_sat *sat);
+
+/*
+ * One request end to end (the plain per-request path): build the tables of
+ * one image, evaluate n window queries, release the tables, and wait.
+ * `image` and every output pointer may be host or device memory; host data
+ * is staged through device memory on `stream`.  Pinned host memory gives
+ * asynchronous copies.  Returns after all results are in place.
+ */
+swa_status swa_analyze(const void *image, int64_t rows, int64_t cols,
+                       int64_t pitch_bytes, swa_dtype dtype,
+                       const swa_window *windows, int32_t n, swa_stream stream);
+
+/* Process-wide cap on the device bytes this library holds (tables, scratch
+ * and staging) on each device; a request beyond it fails with SWA_ENOMEM.
+ * A negative value removes the cap (the default). */
+swa_status swa_set_memory_limit(int64_t bytes);
+
+/* Bytes this library currently holds on the current device. */
+int64_t swa_memory_in_use(void);
+
+/* Return cached device memory above `keep_bytes` to the system. */
+swa_status swa_trim(int64_t keep_bytes);
+
+/* Static description of a status code. */
+const char *swa_status_str(swa_status s);
+
+/* Description of the last error on the calling host thread ("" if none). */
+const char *swa_last_error(void);
+
+/* Kernels this library launched in the process so far (all devices). */
+int64_t swa_launch_count(void);
+
+/* Per-kernel device time, for measurement.  Between swa_profile_begin and
+ * swa_profile_end every kernel the library launches is bracketed by two CUDA
+ * events on its own stream.  swa_profile_end waits for those events, writes
+ * at most `max` entries (one per kernel name: launches, summed and largest
+ * duration) and returns the number of distinct kernels, or -1 on a CUDA
+ * error.  Profiling is process-wide; do not nest it. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+    double max_ms;
+} swa_kernel_time;
+swa_status swa_profile_begin(void);
+int32_t swa_profile_end(swa_kernel_time *out, int32_t max);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int32_t swa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWA_H */

@@ -14,6 +14,7 @@ definitions and the paper sections they follow):
 - ``window_sat``     integral-image SWA, four lookups (Sections II-B, III-B)
 - ``window_sliding`` DP-naive-SWA read as separable moving sums (Section IV-A)
 - ``window_one``     one window by the definition (sampled checks at any size)
+- ``window_sat_rows`` integral-image SWA for selected output rows
 - ``stats_from_moments`` mean and population std from exact integer moments
 """
 from __future__ import annotations
@@ -67,6 +68,8 @@ def _load():
         lib.oracle_window_sat.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, i64,
                                           vp, vp, vp, i64]
         lib.oracle_total.argtypes = [vp, i64, i64, i64, ci, P(u64), P(u64)]
+        lib.oracle_window_sat_rows.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, i64,
+                                               vp, i64, vp, vp, vp, i64]
         _lib = lib
     return _lib
 
@@ -185,6 +188,21 @@ def window_sat(S, Q, wh, ww, sy=1, sx=1, outputs=("sum", "mean", "std")):
     s, m, d = _outputs(R, C, outputs)
     _check(_load().oracle_window_sat(S.ctypes.data, _p(Q), c, r, c, wh, ww, sy, sx,
                                      _p(s), _p(m), _p(d), C), "window_sat")
+    return {k: v for k, v in (("sum", s), ("mean", m), ("std", d)) if v is not None}
+
+
+def window_sat_rows(S, Q, wh, ww, sy, sx, out_rows, outputs=("sum", "mean", "std")):
+    """Integral-image SWA for the selected output rows only."""
+    S = np.ascontiguousarray(S, dtype=np.uint64)
+    if Q is not None:
+        Q = np.ascontiguousarray(Q, dtype=np.uint64)
+    r, c = S.shape
+    R, C = window_shape(r, c, wh, ww, sy, sx)
+    rr = np.ascontiguousarray(np.asarray(out_rows, dtype=np.int64))
+    s, m, d = _outputs(len(rr), C, outputs)
+    _check(_load().oracle_window_sat_rows(S.ctypes.data, _p(Q), c, r, c, wh, ww, sy, sx,
+                                          rr.ctypes.data, len(rr), _p(s), _p(m), _p(d), C),
+           "window_sat_rows")
     return {k: v for k, v in (("sum", s), ("mean", m), ("std", d)) if v is not None}
 
 

@@ -326,3 +326,38 @@ int oracle_total(const void *img, int64_t rows, int64_t cols, int64_t pitch,
     if (sumsq) *sumsq = q;
     return OK;
 }
+
+/*
+ * Integral-image SWA for selected output rows only (sampled full-size
+ * checks): row k of the outputs (ld entries apart) receives output row
+ * out_rows[k].  Same lookups as oracle_window_sat.
+ */
+int oracle_window_sat_rows(const uint64_t *S, const uint64_t *Q, int64_t ld_sat,
+                           int64_t rows, int64_t cols, int64_t wh, int64_t ww,
+                           int64_t sy, int64_t sx, const int64_t *out_rows,
+                           int64_t nrows, uint64_t *sum, double *mean, double *std,
+                           int64_t ld)
+{
+    int64_t R, C;
+    if (!S || (std && !Q) || !out_rows) return E_ARG;
+    if (oracle_window_shape(rows, cols, wh, ww, sy, sx, &R, &C) != OK) return E_ARG;
+    if (ld < C || ld_sat < cols) return E_ARG;
+    uint64_t n = (uint64_t)(wh * ww);
+    for (int64_t k = 0; k < nrows; ++k) {
+        int64_t i = out_rows[k];
+        if (i < 0 || i >= R) return E_ARG;
+        for (int64_t j = 0; j < C; ++j) {
+            int64_t y0 = i * sy, x0 = j * sx, y1 = y0 + wh - 1, x1 = x0 + ww - 1;
+            uint64_t s = at(S, ld_sat, y1, x1) - at(S, ld_sat, y0 - 1, x1)
+                       - at(S, ld_sat, y1, x0 - 1) + at(S, ld_sat, y0 - 1, x0 - 1);
+            uint64_t q = 0;
+            if (Q)
+                q = at(Q, ld_sat, y1, x1) - at(Q, ld_sat, y0 - 1, x1)
+                  - at(Q, ld_sat, y1, x0 - 1) + at(Q, ld_sat, y0 - 1, x0 - 1);
+            if (sum) sum[k * ld + j] = s;
+            oracle_stats_from_moments(n, s, q, mean ? &mean[k * ld + j] : NULL,
+                                      std ? &std[k * ld + j] : NULL);
+        }
+    }
+    return OK;
+}

@@ -1,0 +1,422 @@
+// Summed-area table build on the GPU (Section II-B's table; Section III-B's
+// O(r*c)/p parallel cost).
+//
+// Decomposition.  The image is cut into warp tiles of TH rows x 256 columns
+// (one 256-column "slice" per warp, 8 pixels per lane).  For a tile whose
+// top-left pixel is (y0, xs0), every entry of the inclusive table splits into
+// three carries and one tile-local part:
+//
+//   S[y][x] = K + H[y] + V*[x] + lp[y][x]
+//     K     = sum of I over rows < y0, columns < xs0 (the tiles above-left),
+//     H[y]  = sum of I over rows y0..y, columns < xs0 (left row sums, summed
+//             down the tile),
+//     V*[x] = sum over columns xs0..x of V[j], V[j] = sum of I over rows < y0
+//             in column j (the column sums above the tile),
+//     lp    = the tile's own 2-D inclusive prefix sum.
+//
+// This file's two-pass build obtains the carries by reading the image twice:
+// a reduce kernel writes per-tile column sums, row sums and totals; a carry
+// kernel turns them into exclusive scans; the scan kernel re-reads the image
+// and writes S (and Q, the same for I^2).  Table entries are exact uint64;
+// tile-local parts use 32-bit integers where their bounds allow.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "swa_internal.h"
+
+namespace swa {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 8;                 // warps per block in tile kernels
+
+// Tile-local accumulator of squared pixels: 32 bits hold 256 x 128 x 255^2,
+// but uint16 squares need 64 bits.
+template <typename T> struct QAcc { using type = uint32_t; };
+template <> struct QAcc<uint16_t> { using type = uint64_t; };
+
+// Load 8 consecutive pixels of row y starting at column x; pixels at or past
+// `cols` read as 0.  VEC: the image base and pitch are 16-byte aligned, so a
+// full chunk is one 8- or 16-byte load.
+template <typename T, bool VEC>
+__device__ __forceinline__ void load8(const char *__restrict__ img, int64_t pitch,
+                                      int64_t y, int64_t x, int64_t cols,
+                                      uint32_t px[8])
+{
+    const T *row = reinterpret_cast<const T *>(img + y * pitch);
+    if (VEC && x + 8 <= cols) {
+        if (sizeof(T) == 1) {
+            uint2 v = __ldg(reinterpret_cast<const uint2 *>(row + x));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                px[k] = (v.x >> (8 * k)) & 0xffu;
+                px[k + 4] = (v.y >> (8 * k)) & 0xffu;
+            }
+        } else {
+            uint4 v = __ldg(reinterpret_cast<const uint4 *>(row + x));
+            px[0] = v.x & 0xffffu; px[1] = v.x >> 16;
+            px[2] = v.y & 0xffffu; px[3] = v.y >> 16;
+            px[4] = v.z & 0xffffu; px[5] = v.z >> 16;
+            px[6] = v.w & 0xffffu; px[7] = v.w >> 16;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            px[k] = (x + k < cols) ? (uint32_t)__ldg(row + x + k) : 0u;
+    }
+}
+
+template <typename U>
+__device__ __forceinline__ U warp_incl_scan(U v, int lane)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        U t = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) { return __reduce_add_sync(kFull, v); }
+__device__ __forceinline__ uint64_t warp_sum(uint64_t v)
+{
+#pragma unroll
+    for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+
+// Store 8 consecutive table entries of one row (16-byte vector stores when
+// the whole chunk is inside the row).
+__device__ __forceinline__ void store8(uint64_t *__restrict__ dst, int64_t x, int64_t cols,
+                                       const uint64_t v[8])
+{
+    if (x + 8 <= cols) {
+        ulonglong2 *d = reinterpret_cast<ulonglong2 *>(dst + x);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (x + k < cols) dst[x + k] = v[k];
+    }
+}
+
+struct Carries {
+    uint64_t *cs_s, *cs_q;   // [nby][ld]  column sums per band -> V (exclusive over bands)
+    uint64_t *rs_s, *rs_q;   // [nsx][rows] row sums per slice -> LR (exclusive over slices)
+    uint64_t *tt_s, *tt_q;   // [nby][nsx] tile totals; then [nsx][nby] exclusive over slices
+    uint64_t *tk_s, *tk_q;   // [nsx][nby] row-scanned tile totals (transposed)
+};
+
+// ---------------------------------------------------------------- reduce --
+// One warp per tile: column sums (per lane, 8 columns), row sums (warp
+// reductions, kept by lane (row mod 32) and stored 32 rows at a time) and the
+// tile total.
+template <typename T, bool WQ, bool VEC, int TH>
+__global__ void __launch_bounds__(kWarps * 32)
+k_reduce(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
+         int64_t ld, int64_t nby, int64_t nsx, Carries c)
+{
+    using QA = typename QAcc<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (t >= nby * nsx) return;
+    const int64_t b = t / nsx, s = t % nsx;
+    const int64_t y0 = b * TH, y1 = min(rows, y0 + TH);
+    const int64_t x = s * kSliceCols + lane * kPxPerLane;
+
+    uint32_t cs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    QA cq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t keep_s = 0, keep_q = 0, tot_s = 0, tot_q = 0;
+    uint32_t px[8];
+    for (int64_t y = y0; y < y1; ++y) {
+        load8<T, VEC>(img, pitch, y, x, cols, px);
+        uint32_t rs = 0;
+        QA rq = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            cs[k] += px[k];
+            rs += px[k];
+            if (WQ) {
+                QA p2 = (QA)px[k] * (QA)px[k];
+                cq[k] += p2;
+                rq += p2;
+            }
+        }
+        uint64_t row_s = warp_sum(rs);
+        uint64_t row_q = WQ ? (uint64_t)warp_sum(rq) : 0;
+        const int r = (int)(y - y0) & 31;
+        if (lane == r) { keep_s = row_s; keep_q = row_q; }
+        tot_s += row_s;
+        tot_q += row_q;
+        if (r == 31 || y == y1 - 1) {
+            const int64_t yy = y - r + lane;
+            if (yy <= y) {
+                c.rs_s[s * rows + yy] = keep_s;
+                if (WQ) c.rs_q[s * rows + yy] = keep_q;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (x + k < cols) {
+            c.cs_s[b * ld + x + k] = cs[k];
+            if (WQ) c.cs_q[b * ld + x + k] = cq[k];
+        }
+    }
+    if (lane == 0) {
+        c.tt_s[b * nsx + s] = tot_s;
+        if (WQ) c.tt_q[b * nsx + s] = tot_q;
+    }
+}
+
+// ---------------------------------------------------------------- carries --
+// Three independent groups of blocks:
+//   A: per column, exclusive scan of the band column sums down the bands (V);
+//   B: per row, exclusive scan of the slice row sums along the slices (LR);
+//   C: per band, exclusive scan of the tile totals along the slices, written
+//      transposed so the scan kernel can sum it down the bands coalesced.
+// Loads are batched 8 at a time ahead of the dependent running sum.
+template <bool WQ>
+__device__ __forceinline__ void excl_scan_strided(uint64_t *__restrict__ a,
+                                                  uint64_t *__restrict__ q,
+                                                  int64_t n, int64_t stride)
+{
+    uint64_t run_s = 0, run_q = 0;
+    int64_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        uint64_t vs[8], vq[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            vs[k] = a[(i + k) * stride];
+            if (WQ) vq[k] = q[(i + k) * stride];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            a[(i + k) * stride] = run_s;
+            run_s += vs[k];
+            if (WQ) { q[(i + k) * stride] = run_q; run_q += vq[k]; }
+        }
+    }
+    for (; i < n; ++i) {
+        uint64_t vs = a[i * stride];
+        a[i * stride] = run_s;
+        run_s += vs;
+        if (WQ) { uint64_t vq = q[i * stride]; q[i * stride] = run_q; run_q += vq; }
+    }
+}
+
+template <bool WQ>
+__global__ void __launch_bounds__(256)
+k_carry(int64_t rows, int64_t cols, int64_t ld, int64_t nby, int64_t nsx,
+        int64_t nA, int64_t nB, Carries c)
+{
+    const int64_t blk = blockIdx.x;
+    if (blk < nA) {
+        const int64_t x = blk * 256 + threadIdx.x;
+        if (x < cols) excl_scan_strided<WQ>(c.cs_s + x, c.cs_q + x, nby, ld);
+    } else if (blk < nA + nB) {
+        const int64_t y = (blk - nA) * 256 + threadIdx.x;
+        if (y < rows) excl_scan_strided<WQ>(c.rs_s + y, c.rs_q + y, nsx, rows);
+    } else {
+        const int64_t b = (blk - nA - nB) * 256 + threadIdx.x;
+        if (b >= nby) return;
+        uint64_t run_s = 0, run_q = 0;
+        for (int64_t s = 0; s < nsx; ++s) {
+            uint64_t vs = c.tt_s[b * nsx + s];
+            c.tk_s[s * nby + b] = run_s;
+            run_s += vs;
+            if (WQ) {
+                uint64_t vq = c.tt_q[b * nsx + s];
+                c.tk_q[s * nby + b] = run_q;
+                run_q += vq;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ scan --
+// One warp per tile: assemble the carries, then walk the tile's rows keeping
+// per-column running sums, scan each row across the warp and store S (and Q).
+template <typename T, bool WQ, bool VEC, int TH>
+__global__ void __launch_bounds__(kWarps * 32)
+k_scan(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
+       int64_t ld, int64_t nby, int64_t nsx, Carries c, uint64_t *__restrict__ S,
+       uint64_t *__restrict__ Q)
+{
+    using QA = typename QAcc<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (t >= nby * nsx) return;
+    const int64_t b = t / nsx, s = t % nsx;
+    const int64_t y0 = b * TH, y1 = min(rows, y0 + TH);
+    const int64_t x = s * kSliceCols + lane * kPxPerLane;
+
+    // K: exclusive 2-D sum of tile totals above-left = sum over bands < b of
+    // the (already slice-scanned) totals.
+    uint64_t K_s = 0, K_q = 0;
+    for (int64_t bb = lane; bb < b; bb += 32) {
+        K_s += c.tk_s[s * nby + bb];
+        if (WQ) K_q += c.tk_q[s * nby + bb];
+    }
+    K_s = warp_sum(K_s);
+    if (WQ) K_q = warp_sum(K_q);
+
+    // V*: inclusive scan of the column sums above the tile across the slice.
+    uint64_t vs[8], vq[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const bool in = x + k < cols;
+        vs[k] = in ? c.cs_s[b * ld + x + k] : 0;
+        vq[k] = (WQ && in) ? c.cs_q[b * ld + x + k] : 0;
+    }
+#pragma unroll
+    for (int k = 1; k < 8; ++k) { vs[k] += vs[k - 1]; if (WQ) vq[k] += vq[k - 1]; }
+    {
+        uint64_t is = warp_incl_scan(vs[7], lane), es = is - vs[7];
+        uint64_t iq = WQ ? warp_incl_scan(vq[7], lane) : 0, eq = iq - vq[7];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { vs[k] += es + K_s; if (WQ) vq[k] += eq + K_q; }
+    }
+
+    uint32_t cp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    QA cq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t H_s = 0, H_q = 0, lr_s = 0, lr_q = 0;
+    uint32_t px[8], nx[8];
+    if (y0 < y1) load8<T, VEC>(img, pitch, y0, x, cols, nx);
+    for (int64_t y = y0; y < y1; ++y) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) px[k] = nx[k];
+        if (y + 1 < y1) load8<T, VEC>(img, pitch, y + 1, x, cols, nx);
+        const int r = (int)(y - y0) & 31;
+        if (r == 0) {
+            const int64_t yy = y + lane;
+            lr_s = yy < y1 ? c.rs_s[s * rows + yy] : 0;
+            lr_q = (WQ && yy < y1) ? c.rs_q[s * rows + yy] : 0;
+        }
+        H_s += __shfl_sync(kFull, lr_s, r);
+        if (WQ) H_q += __shfl_sync(kFull, lr_q, r);
+
+        uint32_t lp[8];
+        QA lq[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            cp[k] += px[k];
+            lp[k] = cp[k] + (k ? lp[k - 1] : 0u);
+            if (WQ) {
+                cq[k] += (QA)px[k] * (QA)px[k];
+                lq[k] = cq[k] + (k ? lq[k - 1] : (QA)0);
+            }
+        }
+        const uint32_t is = warp_incl_scan(lp[7], lane);
+        const uint64_t base_s = H_s + (uint64_t)(is - lp[7]);
+        uint64_t out[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out[k] = base_s + vs[k] + lp[k];
+        store8(S + y * ld, x, cols, out);
+        if (WQ) {
+            const QA iq = warp_incl_scan(lq[7], lane);
+            const uint64_t base_q = H_q + (uint64_t)(iq - lq[7]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) out[k] = base_q + vq[k] + (uint64_t)lq[k];
+            store8(Q + y * ld, x, cols, out);
+        }
+    }
+}
+
+constexpr int kTH = 128;   // rows per tile (u8 tile-local Q sums stay below 2^32)
+
+template <typename T, bool WQ, bool VEC>
+swa_status launch_twopass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
+                          char *scratch, cudaStream_t st)
+{
+    Carries c;
+    const int64_t nb = p.nby, ns = p.nsx;
+    c.cs_s = reinterpret_cast<uint64_t *>(scratch + p.off_cs);
+    c.cs_q = c.cs_s + nb * p.ld;
+    c.rs_s = reinterpret_cast<uint64_t *>(scratch + p.off_rs);
+    c.rs_q = c.rs_s + ns * p.rows;
+    c.tt_s = reinterpret_cast<uint64_t *>(scratch + p.off_bt);
+    c.tt_q = c.tt_s + nb * ns;
+    c.tk_s = c.tt_q + nb * ns;
+    c.tk_q = c.tk_s + nb * ns;
+    const int64_t tiles = nb * ns;
+    const int64_t blocks = (tiles + kWarps - 1) / kWarps;
+    {
+        LaunchScope ls("sat_reduce", st);
+        k_reduce<T, WQ, VEC, kTH><<<(unsigned)blocks, kWarps * 32, 0, st>>>(
+            img, p.pitch, p.rows, p.cols, p.ld, nb, ns, c);
+    }
+    const int64_t nA = (p.cols + 255) / 256, nB = (p.rows + 255) / 256, nC = (nb + 255) / 256;
+    {
+        LaunchScope ls("sat_carry", st);
+        k_carry<WQ><<<(unsigned)(nA + nB + nC), 256, 0, st>>>(p.rows, p.cols, p.ld, nb, ns,
+                                                              nA, nB, c);
+    }
+    {
+        LaunchScope ls("sat_scan", st);
+        k_scan<T, WQ, VEC, kTH><<<(unsigned)blocks, kWarps * 32, 0, st>>>(
+            img, p.pitch, p.rows, p.cols, p.ld, nb, ns, c, S, Q);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("SAT build launch failed: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    return SWA_OK;
+}
+
+template <typename T>
+swa_status dispatch_twopass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
+                            char *scratch, cudaStream_t st)
+{
+    if (p.with_q)
+        return p.vec ? launch_twopass<T, true, true>(p, img, S, Q, scratch, st)
+                     : launch_twopass<T, true, false>(p, img, S, Q, scratch, st);
+    return p.vec ? launch_twopass<T, false, true>(p, img, S, Q, scratch, st)
+                 : launch_twopass<T, false, false>(p, img, S, Q, scratch, st);
+}
+
+int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
+
+}  // namespace
+
+BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32_t flags,
+                    const void *image)
+{
+    BuildPlan p{};
+    p.rows = rows;
+    p.cols = cols;
+    p.pitch = pitch;
+    p.dtype = dtype;
+    p.with_q = (flags & SWA_WITH_SQ) != 0;
+    p.twopass = true;
+    p.ld = (cols + kLdAlign - 1) / kLdAlign * kLdAlign;
+    p.vec = ((uintptr_t)image % 16 == 0) && (pitch % 16 == 0);
+    p.th = kTH;
+    p.nby = (rows + kTH - 1) / kTH;
+    p.nsx = (cols + kSliceCols - 1) / kSliceCols;
+    int64_t off = 0;
+    p.off_err = off;
+    off = align256(off + 16);
+    p.off_cs = off;
+    off = align256(off + 2 * p.nby * p.ld * 8);
+    p.off_rs = off;
+    off = align256(off + 2 * p.nsx * rows * 8);
+    p.off_bt = off;
+    off = align256(off + 4 * p.nby * p.nsx * 8);
+    p.off_stat = off;
+    p.off_ticket = off;
+    p.scratch_bytes = off;
+    return p;
+}
+
+swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S, uint64_t *Q,
+                        char *scratch, cudaStream_t st)
+{
+    const char *img = static_cast<const char *>(image);
+    if (p.dtype == SWA_U8) return dispatch_twopass<uint8_t>(p, img, S, Q, scratch, st);
+    return dispatch_twopass<uint16_t>(p, img, S, Q, scratch, st);
+}
+
+}  // namespace swa

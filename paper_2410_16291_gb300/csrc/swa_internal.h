@@ -1,0 +1,85 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swa.h"
+
+namespace swa {
+
+constexpr uint64_t kHandleTag = 0x5357414841ULL;   // "SWAHA"
+constexpr uint64_t kFreedTag = 0x5357414644ULL;    // "SWAFD"
+
+// Device error word bits (a uint32 in the handle's scratch).
+constexpr uint32_t kErrTimeout = 1u;
+
+// Table rows are padded to a multiple of this many elements (256 bytes), so
+// that every warp's row segment starts on a full 32-byte sector.
+constexpr int64_t kLdAlign = 32;
+
+// Width of the column slice one warp owns in the SAT build: 32 lanes x 8 px.
+constexpr int kSliceCols = 256;
+constexpr int kPxPerLane = 8;
+
+struct BuildPlan {
+    int64_t rows, cols, ld, pitch;
+    int dtype;            // SWA_U8 / SWA_U16
+    bool with_q;
+    bool vec;             // image base and pitch allow 8-pixel vector loads
+    int th;               // rows per tile
+    int64_t nby, nsx;     // tile bands, column slices
+    // scratch layout (byte offsets inside one allocation)
+    int64_t off_err, off_cs, off_rs, off_bt, off_stat, off_ticket, scratch_bytes;
+    bool twopass;
+};
+
+struct Handle {
+    uint64_t tag;
+    int device;
+    int64_t rows, cols, ld;
+    int dtype;
+    uint32_t flags;
+    uint64_t *S, *Q;          // device tables (Q may be null)
+    char *scratch;            // carries, tile status, error word
+    int64_t scratch_bytes, table_bytes;
+    uint32_t *d_err;          // device error word (inside scratch)
+    cudaStream_t stream;      // home stream
+    cudaEvent_t use_event;    // joins other streams' calls into the home stream
+};
+
+// Memory accounting and the per-device pool.
+cudaError_t dev_alloc(void **p, int64_t bytes, cudaStream_t s, swa_status *st);
+void dev_free(void *p, int64_t bytes, cudaStream_t s);
+void count_launch(int n = 1);
+
+// Brackets one kernel launch with events while profiling is on (see
+// swa_profile_begin); counts the launch either way.
+class LaunchScope {
+  public:
+    LaunchScope(const char *name, cudaStream_t s);
+    ~LaunchScope();
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    int slot_;
+};
+void set_error(const char *fmt, ...);
+
+// SAT build (sat_build.cu).
+BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype,
+                    uint32_t flags, const void *image);
+swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S,
+                        uint64_t *Q, char *scratch, cudaStream_t s);
+
+// Window statistics (window_stats.cu).
+struct WinDesc {
+    int64_t wh, ww, sy, sx, R, C, out_ld;
+    uint32_t outputs;
+    uint64_t *sum;
+    double *mean, *std;
+};
+swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld,
+                          const WinDesc *w, int n, cudaStream_t s);
+
+}  // namespace swa

@@ -1,0 +1,106 @@
+"""The C ABI: the library builds, loads and exports every declared entry
+point, and host-side argument checks answer without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2410_16291_gb300 as swa
+from paper_2410_16291_gb300 import build as swa_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "swa.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    swa_build.build()
+    return swa.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(swa_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_survey_calls():
+    names = declared_functions()
+    for n in ("swa_build_sat", "swa_window_stats", "swa_free", "swa_window_shape",
+              "swa_sat_data", "swa_sync", "swa_status_str"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", swa.LIB_PATH], text=True)
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    # only the ABI is exported (the static CUDA runtime stays hidden)
+    assert all(n.startswith("swa_") for n in exported if not n.startswith("_")), \
+        sorted(n for n in exported if not n.startswith("swa_"))[:10]
+    assert set(swa.SIGNATURES) <= set(declared_functions())
+
+
+def test_status_strings_and_version(L):
+    for s in range(6):
+        assert L.swa_status_str(s)
+    assert L.swa_version() == 10000
+
+
+def test_window_shape_host_only(L):
+    assert swa.window_shape(1024, 1024, 32, 32, 1, 1) == (993, 993)
+    assert swa.window_shape(70000, 85000, 1024, 1024, 16, 16) == (4312, 5249)
+    R, C = ctypes.c_int64(), ctypes.c_int64()
+    for bad in [(10, 10, 11, 1, 1, 1), (10, 10, 1, 11, 1, 1), (10, 10, 2, 2, 0, 1),
+                (0, 10, 1, 1, 1, 1), (10, 10, 0, 1, 1, 1)]:
+        assert L.swa_window_shape(*bad, ctypes.byref(R), ctypes.byref(C)) == swa.SWA_EINVAL
+
+
+def test_build_argument_checks_before_any_device_work(L):
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: every call below fails first
+    assert L.swa_build_sat(None, 10, 10, 10, swa.SWA_U8, 0, None, ctypes.byref(h)) == swa.SWA_EINVAL
+    assert L.swa_build_sat(fake, 0, 10, 10, swa.SWA_U8, 0, None, ctypes.byref(h)) == swa.SWA_EINVAL
+    assert L.swa_build_sat(fake, 10, 10, 9, swa.SWA_U8, 0, None, ctypes.byref(h)) == swa.SWA_EINVAL
+    assert L.swa_build_sat(fake, 10, 10, 19, swa.SWA_U16, 0, None, ctypes.byref(h)) == swa.SWA_EINVAL
+    assert L.swa_build_sat(fake, 10, 10, 10, 3, 0, None, ctypes.byref(h)) == swa.SWA_EINVAL
+    assert L.swa_build_sat(fake, 10, 10, 21, swa.SWA_U16, 0, None, ctypes.byref(h)) == swa.SWA_EINVAL
+    odd = ctypes.c_void_p(0x1001)
+    assert L.swa_build_sat(odd, 10, 10, 20, swa.SWA_U16, 0, None, ctypes.byref(h)) == swa.SWA_EINVAL
+    assert L.swa_build_sat(fake, 10, 10, 10, swa.SWA_U8, 8, None, ctypes.byref(h)) == swa.SWA_EINVAL
+    assert L.swa_build_sat(fake, 10, 10, 10, swa.SWA_U8, 0, None, None) == swa.SWA_EINVAL
+    # the u16 squared table of a 70,000 x 85,000 image could overflow uint64
+    assert L.swa_build_sat(fake, 70000, 85000, 170000, swa.SWA_U16, swa.SWA_WITH_SQ, None,
+                           ctypes.byref(h)) == swa.SWA_EOVERFLOW
+    assert L.swa_build_sat(fake, 184252, 23311, 2 * 23311, swa.SWA_U16, swa.SWA_WITH_SQ, None,
+                           ctypes.byref(h)) == swa.SWA_EOVERFLOW
+    # a memory limit of zero refuses the build before allocating
+    L.swa_set_memory_limit(0)
+    try:
+        assert L.swa_build_sat(fake, 100, 100, 100, swa.SWA_U8, 1, None,
+                               ctypes.byref(h)) == swa.SWA_ENOMEM
+    finally:
+        L.swa_set_memory_limit(-1)
+    assert h.value is None
+
+
+def test_handle_checks(L):
+    assert L.swa_window_stats(None, 2, 2, 1, 1, 1, None, None, None, 1, None) == swa.SWA_EINVAL
+    assert L.swa_sync(None) == swa.SWA_EINVAL
+    assert L.swa_sat_data(None, None, None, None) == swa.SWA_EINVAL
+    bogus = ctypes.c_void_p(0xdeadbeef)
+    assert L.swa_sync(bogus) == swa.SWA_EINVAL          # not a live handle: never read
+    L.swa_free(None)
+    L.swa_free(bogus)                                      # ignored, not dereferenced
+
+
+def test_sat_bytes(L):
+    t, s = ctypes.c_int64(), ctypes.c_int64()
+    assert L.swa_sat_bytes(70000, 85000, swa.SWA_U8, swa.SWA_WITH_SQ, ctypes.byref(t),
+                           ctypes.byref(s)) == swa.SWA_OK
+    ld = (85000 + 31) // 32 * 32
+    assert t.value == 2 * 8 * 70000 * ld
+    assert s.value < t.value // 16

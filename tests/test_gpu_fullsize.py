@@ -1,0 +1,116 @@
+"""Parity at the workloads' full sizes, in the benchmark's launch
+configuration: full tables where host memory allows, otherwise sampled rows
+and windows the oracle computes one by one, plus invariants that hold at any
+size."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2410_16291_gb300 as swa
+import synth
+from gpu_util import f64, require_gpu, to_device, u64
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+RNG = np.random.default_rng(99)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+    from paper_2410_16291_gb300 import build
+    build.build()
+    yield
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    swa.lib().swa_trim(0)
+
+
+def sampled_windows(img, res, windows, n):
+    for (wh, ww, sy, sx), got in zip(windows, res):
+        R, C = got["sum"].shape
+        ii = np.concatenate([[0, R - 1], RNG.integers(0, R, n)])
+        jj = np.concatenate([[0, C - 1], RNG.integers(0, C, n)])
+        gs = u64(got["sum"][ii, jj])
+        gm, gd = f64(got["mean"][ii, jj]), f64(got["std"][ii, jj])
+        for k, (i, j) in enumerate(zip(ii, jj)):
+            s, _, m, d = oracle.window_one(img, int(i) * sy, int(j) * sx, wh, ww)
+            assert gs[k] == s and gm[k] == m and gd[k] == d, (wh, i, j)
+
+
+def test_workload1_20k():
+    """20,000 x 20,000 u8: full S and Q, sampled full output rows and random
+    windows for w = 50, 100, 200 at stride 1."""
+    (im,) = synth.workload(1)
+    img = im.generate()
+    sat = swa.build_sat(to_device(img))
+    wins = [(w.wh, w.ww, w.sy, w.sx) for w in im.windows]
+    res = sat.window_stats(wins)
+    S_ref, Q_ref = oracle.sat(img)
+    S, Q = sat.tables()
+    np.testing.assert_array_equal(u64(S), S_ref)
+    np.testing.assert_array_equal(u64(Q), Q_ref)
+    for (wh, ww, sy, sx), got in zip(wins, res):
+        R, C = got["sum"].shape
+        rows = sorted(set([0, 1, R // 2, R - 1] + list(RNG.integers(0, R, 4))))
+        want = oracle.window_sat_rows(S_ref, Q_ref, wh, ww, sy, sx, rows)
+        np.testing.assert_array_equal(u64(got["sum"][rows]), want["sum"])
+        np.testing.assert_array_equal(f64(got["mean"][rows]), want["mean"])
+        np.testing.assert_array_equal(f64(got["std"][rows]), want["std"])
+    sampled_windows(img, res, wins, 200)
+    sat.free()
+
+
+def test_workload2_70k_by_85k():
+    """70,000 x 85,000 u8 (5.95e9 px, 95 GB of tables): sampled table rows
+    streamed by the oracle, last entries equal the totals, sampled windows and
+    whole output rows by the definition."""
+    (im,) = synth.workload(2)
+    img = im.generate()
+    dev = to_device(img)
+    sat = swa.build_sat(dev)
+    wins = [(w.wh, w.ww, w.sy, w.sx) for w in im.windows]
+    res = sat.window_stats(wins)
+    sat.sync()
+    S, Q = sat.tables()
+    rows = [0, 1, 127, 128, 4095, 35001, 69998, 69999]
+    S_ref, Q_ref = oracle.sat_rows(img, rows)
+    np.testing.assert_array_equal(u64(S[rows]), S_ref)
+    np.testing.assert_array_equal(u64(Q[rows]), Q_ref)
+    tot_s, tot_q = oracle.total(img)
+    assert int(S_ref[-1, -1]) == tot_s and int(Q_ref[-1, -1]) == tot_q
+    sampled_windows(img, res, wins, 100)
+    # one whole output row of the 256 window by the definition
+    got = res[0]
+    i = got["sum"].shape[0] - 1
+    want = oracle.window_brute(img[i * 16:i * 16 + 256], 256, 256, 16, 16)
+    np.testing.assert_array_equal(u64(got["sum"][i:i + 1]), want["sum"])
+    np.testing.assert_array_equal(f64(got["mean"][i:i + 1]), want["mean"])
+    np.testing.assert_array_equal(f64(got["std"][i:i + 1]), want["std"])
+    del S, Q
+    sat.free()
+
+
+def test_u16_all_max_at_the_overflow_edge():
+    """The largest uint16 image whose squared table fits (7809 x 550019 px,
+    all 65535): last entries are r c 65535 and r c 65535^2 (just below 2^64),
+    and sampled entries are (y+1)(x+1) times the pixel (square)."""
+    import torch
+    r, c = 7809, 550019
+    dev = torch.full((r, c), -1, dtype=torch.int16, device="cuda")   # 0xFFFF
+    sat = swa.build_sat(dev)
+    S, Q = sat.tables()
+    v = 65535
+    assert int(u64(S[-1:, -1:])[0, 0]) == r * c * v
+    assert int(u64(Q[-1:, -1:])[0, 0]) == r * c * v * v
+    ys = RNG.integers(0, r, 50)
+    xs = RNG.integers(0, c, 50)
+    gs, gq = u64(S[ys, xs]), u64(Q[ys, xs])
+    for k in range(50):
+        n = (int(ys[k]) + 1) * (int(xs[k]) + 1)
+        assert int(gs[k]) == n * v and int(gq[k]) == n * v * v
+    (o,) = sat.window_stats([(7809, 550019, 1, 1)])
+    assert int(u64(o["sum"])[0, 0]) == r * c * v
+    assert f64(o["std"])[0, 0] == 0.0 and f64(o["mean"])[0, 0] == float(v)
+    del S, Q, dev
+    sat.free()

@@ -1,0 +1,180 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Summed-area tables and window sums must match bit for bit; mean and std are
+formed from the same exact integer moments with correctly rounded IEEE
+operations on both sides, so they are compared bit for bit as well (the
+contract's bar is 1e-12 relative; a bit mismatch is still reported with its
+relative error).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2410_16291_gb300 as swa
+import synth
+from gpu_util import f64, require_gpu, to_device, u64
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-12
+RNG = np.random.default_rng(2024)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+    from paper_2410_16291_gb300 import build
+    build.build()
+    yield
+    import torch
+    torch.cuda.synchronize()
+
+
+def rand_img(r, c, dtype, hi=None):
+    hi = hi if hi is not None else (256 if dtype == np.uint8 else 65536)
+    return RNG.integers(0, hi, size=(r, c), dtype=np.int64).astype(dtype)
+
+
+def assert_close_bits(got, want, what):
+    """Bit-exact comparison; on failure report the worst relative error."""
+    if np.array_equal(got, want):
+        return
+    rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+    bad = np.argwhere(got != want)
+    pytest.fail("%s: %d mismatches, worst rel %.3g at %s (got %r want %r)" % (
+        what, len(bad), rel.max(), bad[0], got[tuple(bad[0])], want[tuple(bad[0])]))
+
+
+def check_tables(sat, img, with_sq=True):
+    S_ref, Q_ref = oracle.sat(img, with_sq=with_sq)
+    S, Q = sat.tables()
+    np.testing.assert_array_equal(u64(S), S_ref)
+    if with_sq:
+        np.testing.assert_array_equal(u64(Q), Q_ref)
+    else:
+        assert Q is None
+    return S_ref, Q_ref
+
+
+def check_windows(sat, S_ref, Q_ref, windows, outputs=("sum", "mean", "std")):
+    res = sat.window_stats(windows, outputs=outputs)
+    for (wh, ww, sy, sx), got in zip(windows, res):
+        want = oracle.window_sat(S_ref, Q_ref, wh, ww, sy, sx, outputs=outputs)
+        if "sum" in outputs:
+            np.testing.assert_array_equal(u64(got["sum"]), want["sum"])
+        for k in ("mean", "std"):
+            if k in outputs:
+                g = f64(got[k])
+                assert np.allclose(g, want[k], rtol=REL_TOL, atol=0), k
+                assert_close_bits(g, want[k], "%s w=%dx%d s=%dx%d" % (k, wh, ww, sy, sx))
+
+
+SHAPES = [(1, 1), (1, 300), (300, 1), (7, 9), (128, 256), (129, 257), (255, 511),
+          (383, 769), (1000, 1031)]
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("twopass", [False, True])
+def test_tables_bitexact(dtype, shape, twopass):
+    img = rand_img(*shape, dtype)
+    sat = swa.build_sat(to_device(img), with_sq=True, twopass=twopass)
+    check_tables(sat, img)
+    sat.sync()
+    sat.free()
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("pad,offset", [(5, 1), (13, 0), (0, 3)])
+def test_tables_pitched_and_unaligned(dtype, pad, offset):
+    """Row pitch larger than the width and a base address off 16-byte
+    alignment take the scalar-load path; results must not change."""
+    img = rand_img(301, 517, dtype)
+    dev = to_device(img, pad_cols=pad, offset_px=offset)
+    sat = swa.build_sat(dev, with_sq=True)
+    check_tables(sat, img)
+    sat.free()
+
+
+def test_sum_only_table_has_no_q():
+    img = rand_img(200, 333, np.uint8)
+    sat = swa.build_sat(to_device(img), with_sq=False)
+    S_ref, _ = check_tables(sat, img, with_sq=False)
+    check_windows(sat, S_ref, None, [(5, 7, 1, 1), (200, 333, 1, 1)], outputs=("sum", "mean"))
+    with pytest.raises(swa.SwaError):
+        sat.window_stats([(5, 5, 1, 1)], outputs=("std",))
+    sat.free()
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_windows_bitexact(dtype):
+    img = rand_img(389, 611, dtype)
+    sat = swa.build_sat(to_device(img))
+    S_ref, Q_ref = check_tables(sat, img)
+    windows = [(1, 1, 1, 1), (2, 3, 1, 1), (32, 32, 1, 1), (50, 50, 1, 1), (17, 29, 3, 5),
+               (100, 100, 16, 16), (389, 611, 1, 1), (389, 1, 7, 1), (1, 611, 1, 9)]
+    check_windows(sat, S_ref, Q_ref, windows)
+    sat.free()
+
+
+def test_windows_closed_forms():
+    """Constant image: mean exact, std exactly 0; checkerboard {0, a}, even w:
+    std exactly a/2."""
+    const = np.full((300, 300), 171, np.uint8)
+    sat = swa.build_sat(to_device(const))
+    (o,) = sat.window_stats([(25, 25, 1, 1)])
+    assert (u64(o["sum"]) == 171 * 625).all()
+    assert (f64(o["mean"]) == 171.0).all() and (f64(o["std"]) == 0.0).all()
+    a = 60000
+    cb = ((np.indices((300, 300)).sum(0) % 2) * a).astype(np.uint16)
+    sat = swa.build_sat(to_device(cb))
+    (o,) = sat.window_stats([(8, 8, 1, 1)])
+    assert (f64(o["std"]) == a / 2).all() and (f64(o["mean"]) == a / 2).all()
+
+
+def test_window_on_another_stream():
+    """The build runs on one stream and the windows on another; the library
+    orders them."""
+    import torch
+    img = rand_img(700, 900, np.uint8)
+    dev = to_device(img)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s1):
+        sat = swa.build_sat(dev, stream=s1)
+    (o,) = sat.window_stats([(40, 40, 1, 1)], stream=s2)
+    s2.synchronize()
+    S_ref, Q_ref = oracle.sat(img)
+    want = oracle.window_sat(S_ref, Q_ref, 40, 40, 1, 1)
+    np.testing.assert_array_equal(u64(o["sum"]), want["sum"])
+    sat.free()
+
+
+def test_analyze_host_buffers_match_device_path():
+    """swa_analyze with pinned host input and host outputs equals the device
+    path."""
+    import torch
+    img = rand_img(513, 1025, np.uint16)
+    wins = [(31, 31, 1, 1), (64, 64, 4, 4)]
+    host = torch.from_numpy(img.view(np.int16)).pin_memory()
+    res = swa.analyze(host, wins)
+    S_ref, Q_ref = oracle.sat(img)
+    for (wh, ww, sy, sx), got in zip(wins, res):
+        want = oracle.window_sat(S_ref, Q_ref, wh, ww, sy, sx)
+        assert not got["sum"].is_cuda
+        np.testing.assert_array_equal(got["sum"].view(torch.int64).numpy().view(np.uint64),
+                                      want["sum"])
+        np.testing.assert_array_equal(got["mean"].numpy(), want["mean"])
+        np.testing.assert_array_equal(got["std"].numpy(), want["std"])
+
+
+def test_workload0_cell_mask():
+    """1024x1024 cell-centroid mask, window 32 stride 1, sum only, against the
+    naive definition."""
+    (im,) = synth.workload(0)
+    img = im.generate()
+    sat = swa.build_sat(to_device(img), with_sq=False)
+    (o,) = sat.window_stats([(32, 32, 1, 1)], outputs=("sum",))
+    want = oracle.window_brute(img, 32, 32, 1, 1, outputs=("sum",))["sum"]
+    np.testing.assert_array_equal(u64(o["sum"]), want)
+    assert o["sum"].shape == (993, 993)
+    sat.free()

@@ -255,3 +255,13 @@ def test_sliding_matches_brute_on_cfg0_crop():
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(a, c)
     np.testing.assert_array_equal(a, numpy_window_sums(img, 32, 32, 1, 1))
+
+
+def test_window_sat_rows_equals_full():
+    img = rand_img(40, 33, np.uint16)
+    S, Q = oracle.sat(img)
+    full = oracle.window_sat(S, Q, 6, 5, 2, 3)
+    rows = [0, 3, full["sum"].shape[0] - 1]
+    part = oracle.window_sat_rows(S, Q, 6, 5, 2, 3, rows)
+    for k in ("sum", "mean", "std"):
+        np.testing.assert_array_equal(part[k], full[k][rows])
