@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=0,
                     help="rows of the CPU-baseline sample (0: sized to ~10 s)")
     ap.add_argument("--twopass", action="store_true", help="force the two-pass SAT build")
+    ap.add_argument("--shape", default="",
+                    help="custom u8 image RxC (profiling cases), e.g. 8192x8192")
+    ap.add_argument("--windows", default="",
+                    help="custom windows w/stride list, e.g. 100/1,256/16")
     return ap.parse_args()
 
 
@@ -183,19 +187,45 @@ def cpu_baseline(im, windows, rows):
     def rows_fn(n):
         return synth.intensity_u8(n, im.cols, im.seed, synth.cluster_count(n, im.cols))
     if rows <= 0:
-        px, _, dt = oracle_sample(rows_fn, im.cols, windows, 256)
-        rows = int(256 * min(20.0, 12.0 / max(dt, 1e-3)))
-        rows = max(1024, min(rows, im.rows, 16384))
+        probe = max(1024, max(w[0] for w in windows))
+        px, _, dt = oracle_sample(rows_fn, im.cols, windows, probe)
+        rows = int(probe * 10.0 / max(dt, 1e-3))          # about 10 s of oracle work
+        free = None
         try:
             import psutil
             free = psutil.virtual_memory().available
-            rows = max(1024, min(rows, int(free * 0.4 / (17 * im.cols))))
         except ImportError:
-            pass
+            try:
+                with open("/proc/meminfo") as f:
+                    for line in f:
+                        if line.startswith("MemAvailable:"):
+                            free = int(line.split()[1]) * 1024
+            except OSError:
+                pass
+        if free:
+            rows = min(rows, int(free * 0.3 / (18 * im.cols)))
+        rows = max(probe, min(rows, im.rows))
     px, outs, dt = oracle_sample(rows_fn, im.cols, windows, rows)
     return {"value": px / dt / 1e9, "unit": "Gpx/s", "cores": 1, "kind": "oracle",
             "sample": "%d x %d rows of the workload's generator (%.2e px), tables + the "
                       "workload's windows that fit, serial C, %.1f s" % (rows, im.cols, px, dt)}
+
+
+def workload_of(args):
+    """The benchmark image: a standard workload, or a custom u8 image for
+    profiling cases (--shape / --windows)."""
+    import synth
+    if args.shape:
+        r, c = (int(v) for v in args.shape.lower().split("x"))
+        wins = [synth.Window(int(w), int(w), int(s), int(s)) for w, s in
+                (x.split("/") for x in (args.windows or "100/1").split(","))]
+        return synth.Image(r, c, "u8", "intensity", synth.DEFAULT_SEED + 17,
+                           synth.cluster_count(r, c), wins)
+    (im,) = synth.workload(args.workload)
+    if args.windows:
+        im.windows = [synth.Window(int(w), int(w), int(s), int(s)) for w, s in
+                      (x.split("/") for x in args.windows.split(","))]
+    return im
 
 
 def run_reference(args, rank, world):
@@ -204,7 +234,7 @@ def run_reference(args, rank, world):
     import synth
     if rank != 0:
         return
-    (im,) = synth.workload(args.workload)
+    im = workload_of(args)
     windows = [(w.wh, w.ww, w.sy, w.sx) for w in im.windows]
     rows = max(w[0] for w in windows)
     rows = max(rows, 1024)
@@ -257,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         import torch.distributed as td
 
-    (im,) = synth.workload(args.workload)
+    im = workload_of(args)
     windows = [(w.wh, w.ww, w.sy, w.sx) for w in im.windows]
     px = im.pixels
     host = torch.empty((im.rows, im.cols), dtype=torch.uint8, pin_memory=True)

@@ -205,6 +205,13 @@ typedef struct {
 swa_status swa_profile_begin(void);
 int32_t swa_profile_end(swa_kernel_time *out, int32_t max);
 
+/* Test hooks (process-wide bit set, 0 = none).  SWA_HOOK_STALL_TILE0: in the
+ * single-pass build the tile taken first never publishes its carries, so
+ * every other tile's bounded wait expires (after about 2 s) and swa_sync
+ * returns SWA_ETIMEOUT; the kernel still exits.  For failure-path tests. */
+enum { SWA_HOOK_STALL_TILE0 = 1u };
+swa_status swa_set_test_hooks(uint32_t hooks);
+
 /* ABI version: major * 10000 + minor * 100 + patch. */
 int32_t swa_version(void);
 

@@ -68,6 +68,8 @@ def _load():
         lib.oracle_window_sat.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, i64,
                                           vp, vp, vp, i64]
         lib.oracle_total.argtypes = [vp, i64, i64, i64, ci, P(u64), P(u64)]
+        lib.oracle_stats_bulk.argtypes = [vp, vp, vp, i64, vp, vp]
+        lib.oracle_stats_bulk.restype = None
         lib.oracle_window_sat_rows.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, i64,
                                                vp, i64, vp, vp, vp, i64]
         _lib = lib
@@ -107,6 +109,16 @@ def stats_from_moments(n: int, sw: int, qw: int):
     m, s = ctypes.c_double(), ctypes.c_double()
     _load().oracle_stats_from_moments(n, sw, qw, ctypes.byref(m), ctypes.byref(s))
     return m.value, s.value
+
+
+def stats_bulk(n, sw, qw):
+    """stats_from_moments over uint64 arrays: (mean, std) float64 arrays."""
+    n, sw, qw = (np.ascontiguousarray(a, dtype=np.uint64) for a in (n, sw, qw))
+    m = np.empty(len(n), np.float64)
+    s = np.empty(len(n), np.float64)
+    _load().oracle_stats_bulk(n.ctypes.data, sw.ctypes.data, qw.ctypes.data, len(n),
+                              m.ctypes.data, s.ctypes.data)
+    return m, s
 
 
 def sat(img, with_sq: bool = True):

@@ -361,3 +361,11 @@ int oracle_window_sat_rows(const uint64_t *S, const uint64_t *Q, int64_t ld_sat,
     }
     return OK;
 }
+
+/* oracle_stats_from_moments over arrays (a plain loop; for bulk tests). */
+void oracle_stats_bulk(const uint64_t *n, const uint64_t *sw, const uint64_t *qw,
+                       int64_t count, double *mean, double *std)
+{
+    for (int64_t i = 0; i < count; ++i)
+        oracle_stats_from_moments(n[i], sw[i], qw[i], &mean[i], &std[i]);
+}

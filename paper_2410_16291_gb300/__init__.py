@@ -20,6 +20,7 @@ SWA_OK, SWA_EINVAL, SWA_EOVERFLOW, SWA_ENOMEM, SWA_ECUDA, SWA_ETIMEOUT = range(6
 SWA_WITH_SQ, SWA_TWOPASS = 1, 2
 SWA_OUT_SUM, SWA_OUT_MEAN, SWA_OUT_STD = 1, 2, 4
 SWA_MAX_WINDOWS = 64
+SWA_HOOK_STALL_TILE0 = 1
 
 #: C function name -> (restype, argtypes)
 _I64, _U64, _U32, _I32, _VP = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
@@ -59,6 +60,7 @@ SIGNATURES = {
     "swa_launch_count": (_I64, []),
     "swa_version": (_I32, []),
     "swa_profile_begin": (ctypes.c_int, []),
+    "swa_set_test_hooks": (ctypes.c_int, [_U32]),
     "swa_profile_end": (_I32, [_P(swa_kernel_time), _I32]),
 }
 
@@ -150,8 +152,10 @@ class SAT:
     def window_stats(self, windows, outputs=("sum", "mean", "std"), stream=None, out=None):
         """Evaluate windows [(wh, ww, sy, sx), ...] in one launch sequence.
 
-        Returns a list of dicts of device tensors (R x C each).  ``out`` may
-        supply preallocated dicts of tensors (contiguous rows, any row stride).
+        Returns a list of dicts of device tensors (R x C each): "sum" is an
+        int64 tensor holding the uint64 sums' bit patterns (torch has few
+        uint64 operations), "mean" and "std" are float64.  ``out`` may supply
+        preallocated dicts of tensors (contiguous rows, any row stride).
         """
         import torch
         if len(windows) > SWA_MAX_WINDOWS:
@@ -173,7 +177,7 @@ class SAT:
             else:
                 o = {}
                 if mask & SWA_OUT_SUM:
-                    o["sum"] = torch.empty((R, C), dtype=torch.uint64, device=dev)
+                    o["sum"] = torch.empty((R, C), dtype=torch.int64, device=dev)
                 if mask & SWA_OUT_MEAN:
                     o["mean"] = torch.empty((R, C), dtype=torch.float64, device=dev)
                 if mask & SWA_OUT_STD:
@@ -261,7 +265,7 @@ def analyze(image, windows, outputs=("sum", "mean", "std"), out=None, stream=Non
             kw = dict(device=image.device, pin_memory=not image.is_cuda)
             o = {}
             if mask & SWA_OUT_SUM:
-                o["sum"] = torch.empty((R, C), dtype=torch.uint64, **kw)
+                o["sum"] = torch.empty((R, C), dtype=torch.int64, **kw)
             if mask & SWA_OUT_MEAN:
                 o["mean"] = torch.empty((R, C), dtype=torch.float64, **kw)
             if mask & SWA_OUT_STD:

@@ -1,0 +1,290 @@
+// Correctly rounded (round-to-nearest-even) double results of the window
+// statistics without the FP64 divide and square-root sequences, whose
+// throughput on GB300 is ~60 G/s per GPU (measured) against ~37 T/s for FP32.
+//
+//   mean = RN( RN(Sw) / n )
+//   std  = RN( RN( sqrt( RN(D) ) ) / n ),   D = n*Qw - Sw^2 (exact, 128-bit)
+//
+// which is, operation for operation, (double)Sw / (double)n and
+// sqrt((double)D) / (double)n in IEEE double arithmetic.  Every step below
+// produces the exactly rounded result from integer arithmetic:
+//   - integer -> double: keep the top 53 bits, round on the guard bit with
+//     the OR of the discarded bits as sticky bit;
+//   - division by the window area n (a launch constant, n < 2^32): an 86-bit
+//     numerator divided by n with two 2-word-by-1-word steps of Moller and
+//     Granlund's division by invariant integers ("Improved division by
+//     invariant integers", IEEE Trans. Computers 60(2), 2011, Algorithm 4),
+//     giving a 54- or 55-bit quotient and an exact remainder for the sticky
+//     bit;
+//   - square root: an FP32 reciprocal-square-root seed, two Newton
+//     corrections computed from exact integer residuals N - R^2, then an
+//     exact floor correction and rounding by comparing the remainder with R
+//     (sqrt(N) > R + 1/2  <=>  N - R^2 > R for integers).
+// The functions are __host__ __device__ so a CPU test can compare them with
+// the host's IEEE arithmetic bit for bit.
+#pragma once
+
+#include <stdint.h>
+#include <math.h>
+
+#if defined(__CUDACC__)
+#define SWA_HD __host__ __device__ __forceinline__
+#else
+#define SWA_HD static inline
+#endif
+
+namespace swa {
+namespace rn {
+
+SWA_HD int clz64(uint64_t x)
+{
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+SWA_HD int clz32(uint32_t x)
+{
+#if defined(__CUDA_ARCH__)
+    return __clz((int)x);
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+SWA_HD double bits_to_double(uint64_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __longlong_as_double((long long)b);
+#else
+    double d;
+    __builtin_memcpy(&d, &b, 8);
+    return d;
+#endif
+}
+
+SWA_HD float bits_to_float(uint32_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float(b);
+#else
+    float f;
+    __builtin_memcpy(&f, &b, 4);
+    return f;
+#endif
+}
+
+SWA_HD float approx_rsqrt(float x)
+{
+#if defined(__CUDA_ARCH__)
+    return rsqrtf(x);
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
+
+SWA_HD int64_t round_to_i64(float x)
+{
+#if defined(__CUDA_ARCH__)
+    return __float2ll_rn(x);
+#else
+    return llrintf(x);
+#endif
+}
+
+// A value sig * 2^exp with sig < 2^53 (sig == 0 means zero).
+struct Fp {
+    uint64_t sig;
+    int exp;
+};
+
+// RN of a 64-bit integer to a 53-bit significand.
+SWA_HD Fp round_u64(uint64_t x)
+{
+    const int L = 64 - clz64(x);
+    if (L <= 53) return Fp{x, 0};
+    const int sh = L - 53;
+    uint64_t m = x >> sh;
+    const uint64_t g = (x >> (sh - 1)) & 1u;
+    const uint64_t st = (x & ((1ull << (sh - 1)) - 1)) != 0;
+    m += g & (st | (m & 1u));
+    int e = sh;
+    if (m >> 53) { m >>= 1; ++e; }
+    return Fp{m, e};
+}
+
+// RN of the 128-bit integer hi*2^64 + lo to a 53-bit significand.
+SWA_HD Fp round_u128(uint64_t hi, uint64_t lo)
+{
+    if (hi == 0) return round_u64(lo);
+    const int L = 128 - clz64(hi);                 // 65..128
+    const int sh = L - 53;                          // 12..75
+    uint64_t m, g, st;
+    if (sh < 64) {
+        m = (hi << (64 - sh)) | (lo >> sh);
+        g = (lo >> (sh - 1)) & 1u;
+        st = (lo & ((1ull << (sh - 1)) - 1)) != 0;
+    } else {
+        const int s2 = sh - 64;                     // 0..11
+        m = hi >> s2;
+        g = s2 ? (hi >> (s2 - 1)) & 1u : lo >> 63;
+        st = s2 ? (((hi & ((1ull << (s2 - 1)) - 1)) | lo) != 0)
+                : ((lo << 1) != 0);
+    }
+    m += g & (st | (m & 1u));
+    int e = sh;
+    if (m >> 53) { m >>= 1; ++e; }
+    return Fp{m, e};
+}
+
+// Divisor n in [1, 2^32): normalized d = n << z (top bit set) and
+// v = floor((2^64 - 1) / d) - 2^32.
+struct Divisor {
+    uint32_t d, v;
+    int z;
+};
+
+static inline Divisor make_divisor(uint32_t n)
+{
+    Divisor D;
+    D.z = n ? __builtin_clz(n) : 0;
+    D.d = n << D.z;
+    D.v = (uint32_t)(0xffffffffffffffffull / D.d - (1ull << 32));
+    return D;
+}
+
+// (u1*2^32 + u0) / d for u1 < d: quotient word, remainder in *r.
+SWA_HD uint32_t div_2by1(uint32_t u1, uint32_t u0, const Divisor &D, uint32_t *r)
+{
+    const uint64_t p = (uint64_t)D.v * u1 + (((uint64_t)u1 << 32) | u0);
+    uint32_t q1 = (uint32_t)(p >> 32) + 1u;
+    const uint32_t q0 = (uint32_t)p;
+    uint32_t rr = u0 - q1 * D.d;
+    if (rr > q0) { --q1; rr += D.d; }
+    if (rr >= D.d) { ++q1; rr -= D.d; }
+    *r = rr;
+    return q1;
+}
+
+// Bits of RN(a * 2^aexp / n), 1 <= a < 2^53, n < 2^32 as a Divisor.
+SWA_HD uint64_t div_rn(uint64_t a, int aexp, const Divisor &D)
+{
+    if (a == 0) return 0;
+    const int la = 64 - clz64(a);
+    const int s = 86 - la;                         // a << s has 86 bits
+    uint64_t hi, lo;
+    if (s >= 64) { hi = a << (s - 64); lo = 0; }
+    else { hi = a >> (64 - s); lo = a << s; }
+    uint32_t r = (uint32_t)hi;                     // < 2^22 < d
+    const uint32_t q1 = div_2by1(r, (uint32_t)(lo >> 32), D, &r);
+    const uint32_t q0 = div_2by1(r, (uint32_t)lo, D, &r);
+    uint64_t Q = ((uint64_t)q1 << 32) | q0;        // in [2^53, 2^55)
+    uint64_t sticky = r != 0;
+    int e = 0;
+    if (Q >> 54) { sticky |= Q & 1u; Q >>= 1; e = 1; }
+    uint64_t M = Q >> 1;
+    const uint64_t g = Q & 1u;
+    M += g & (sticky | (M & 1u));
+    if (M >> 53) { M >>= 1; ++e; }
+    const int sh = s - D.z;                        // value = Q * 2^(aexp - sh)
+    const int E = 53 + e - sh + aexp;              // unbiased exponent
+    return ((uint64_t)(E + 1023) << 52) | (M & ((1ull << 52) - 1));
+}
+
+// 128-bit N - R*R for R < 2^54, as (hi, lo) two's complement.
+SWA_HD void residual(uint64_t Nhi, uint64_t Nlo, uint64_t R, int64_t *rhi, uint64_t *rlo)
+{
+    const uint32_t l = (uint32_t)R, h = (uint32_t)(R >> 32);
+    const uint64_t ll = (uint64_t)l * l, hl = (uint64_t)h * l, hh = (uint64_t)h * h;
+    // R^2 = hh*2^64 + 2*hl*2^32 + ll
+    const uint64_t mid_lo = hl << 33, mid_hi = hl >> 31;
+    uint64_t sq_lo = ll + mid_lo;
+    uint64_t sq_hi = hh + mid_hi + (sq_lo < ll);
+    const uint64_t lo = Nlo - sq_lo;
+    const uint64_t hi = Nhi - sq_hi - (Nlo < sq_lo);
+    *rhi = (int64_t)hi;
+    *rlo = lo;
+}
+
+// RN(sqrt(sig * 2^exp)) for 1 <= sig < 2^53.
+SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
+{
+    const int L = 64 - clz64(sig);
+    uint64_t Mx = sig << (53 - L);                 // [2^52, 2^53)
+    int E = exp - (53 - L);
+    if (E & 1) { Mx <<= 1; E -= 1; }              // [2^52, 2^54), E even
+    const uint64_t Nhi = Mx >> 12, Nlo = Mx << 52; // N = Mx * 2^52
+    // FP32 seed: y ~ 1/sqrt(Mx); R0 ~ sqrt(N) = sqrt(Mx) * 2^26.
+    const int LM = 64 - clz64(Mx);                 // 53 or 54
+    const float fx = bits_to_float(((uint32_t)(LM - 1 + 127) << 23) |
+                                   ((uint32_t)(Mx >> (LM - 24)) & 0x7fffffu));
+    const float y = approx_rsqrt(fx);
+    uint64_t R = (uint64_t)round_to_i64(fx * y * 67108864.0f);    // 2^26
+    // Two Newton corrections R += (N - R^2) / (2R), the quotient from FP32.
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        int64_t rh;
+        uint64_t rl;
+        residual(Nhi, Nlo, R, &rh, &rl);
+        // (rh:rl) >> 32 fits int64 (|N - R^2| < 2^95)
+        const int64_t top = (int64_t)(((uint64_t)rh << 32) | (rl >> 32));
+        const float dlt = (float)top * y * 32.0f;   // * 2^32 / 2^27
+        R = (uint64_t)((int64_t)R + round_to_i64(dlt));
+    }
+    // Exact floor: 0 <= N - R^2 <= 2R.
+    int64_t rh;
+    uint64_t rl;
+    residual(Nhi, Nlo, R, &rh, &rl);
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        if (rh < 0) {                              // R too large
+            --R;
+            residual(Nhi, Nlo, R, &rh, &rl);
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+        // rem > 2R  <=>  R too small
+        const uint64_t twoR = 2 * R;
+        if (rh > 0 || (rh == 0 && rl > twoR)) {
+            ++R;
+            residual(Nhi, Nlo, R, &rh, &rl);
+        }
+    }
+    // Round to nearest: up iff rem > R (rem <= 2R < 2^55, so rh == 0).
+    R += (rh == 0 && rl > R) ? 1u : 0u;
+    int e = E / 2 - 26;
+    if (R >> 53) { R >>= 1; ++e; }
+    return Fp{R, e};
+}
+
+// mean and std of one window from its exact moments (n < 2^32, n >= 1).
+SWA_HD double mean_rn(uint64_t sw, const Divisor &D)
+{
+    const Fp a = round_u64(sw);
+    return bits_to_double(div_rn(a.sig, a.exp, D));
+}
+
+SWA_HD double std_rn(uint64_t n, uint64_t sw, uint64_t qw, const Divisor &D)
+{
+    // D = n*qw - sw^2 (exact, >= 0)
+    const uint64_t a_lo = n * qw;
+#if defined(__CUDA_ARCH__)
+    const uint64_t a_hi = __umul64hi(n, qw);
+    const uint64_t b_lo = sw * sw, b_hi = __umul64hi(sw, sw);
+#else
+    const unsigned __int128 A = (unsigned __int128)n * qw, B = (unsigned __int128)sw * sw;
+    const uint64_t a_hi = (uint64_t)(A >> 64), b_lo = (uint64_t)B, b_hi = (uint64_t)(B >> 64);
+#endif
+    const uint64_t d_lo = a_lo - b_lo;
+    const uint64_t d_hi = a_hi - b_hi - (a_lo < b_lo);
+    if ((d_hi | d_lo) == 0) return 0.0;
+    const Fp d = round_u128(d_hi, d_lo);
+    const Fp s = sqrt_rn(d.sig, d.exp);
+    return bits_to_double(div_rn(s.sig, s.exp, D));
+}
+
+}  // namespace rn
+}  // namespace swa

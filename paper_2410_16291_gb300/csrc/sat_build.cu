@@ -14,7 +14,8 @@
 //             in column j (the column sums above the tile),
 //     lp    = the tile's own 2-D inclusive prefix sum.
 //
-// This file's two-pass build obtains the carries by reading the image twice:
+// The default build is a single pass with decoupled look-back (k_onepass
+// below).  The two-pass build obtains the carries by reading the image twice:
 // a reduce kernel writes per-tile column sums, row sums and totals; a carry
 // kernel turns them into exclusive scans; the scan kernel re-reads the image
 // and writes S (and Q, the same for I^2).  Table entries are exact uint64;
@@ -377,6 +378,405 @@ swa_status dispatch_twopass(const BuildPlan &p, const char *img, uint64_t *S, ui
                  : launch_twopass<T, false, false>(p, img, S, Q, scratch, st);
 }
 
+
+// ------------------------------------------------------------- one pass --
+// Single-pass build with decoupled look-back.  Warps take tiles in row-major
+// ticket order (an atomic counter, so every smaller ticket belongs to a warp
+// that is already running).  A warp stages its tile in shared memory, reduces
+// it, and publishes two aggregates:
+//   vertical   (per tile column slice): the tile's 256 column sums;
+//   horizontal (per tile band): the tile's row sums and the total of the
+//              column sums above it (the corner term K of the tiles to its
+//              right).
+// It then looks back up its slice for the column carries V (summing
+// aggregates until a tile with an inclusive prefix is found), publishes its
+// own inclusive column prefix, looks back left along its band for the row
+// carries LR and K the same way, publishes its inclusive row prefix, and
+// finally scans the staged tile and writes S and Q.  Every wait is bounded by
+// a time limit; on expiry the warp sets the error word and all warps stop.
+constexpr uint32_t kAgg = 1u, kInc = 2u;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
+
+struct OnePass {
+    const char *img;
+    int64_t pitch, rows, cols, ld, nby, nsx;
+    uint64_t *S, *Q;
+    uint32_t *ticket, *err;
+    uint32_t *flag_v, *flag_h;        // [tiles]
+    uint64_t *agg_v, *inc_v;          // [tiles][2][256]
+    uint64_t *agg_h, *inc_h;          // [tiles][2*TH + 2]
+    uint32_t stall_tile0;             // test hook: ticket 0 publishes nothing
+};
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until *flag is non-zero in every lane; returns it, or 0 if the error
+// word is set (by this wait timing out or by another warp).
+__device__ __noinline__ uint32_t wait_flag(const uint32_t *flag, uint32_t *err)
+{
+    uint32_t v = ld_acquire(flag);
+    if (__all_sync(kFull, v != 0)) return __shfl_sync(kFull, v, 0);
+    const uint64_t t0 = global_ns();
+    unsigned ns = 64;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 2048) ns <<= 1;
+        v = ld_acquire(flag);
+        if (__all_sync(kFull, v != 0)) return __shfl_sync(kFull, v, 0);
+        if (*(volatile uint32_t *)err) return 0;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            if ((threadIdx.x & 31) == 0) atomicOr(err, kErrTimeout);
+            __syncwarp();
+            return 0;
+        }
+    }
+}
+
+// Every lane has written its part of a record; make it visible, then flag it.
+__device__ __forceinline__ void publish(uint32_t *flag, uint32_t v)
+{
+    __threadfence();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) st_release(flag, v);
+}
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *g)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *g)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(g) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// Unpack the 8 staged pixels of one lane for one row.
+template <typename T>
+__device__ __forceinline__ void smem8(const T *row, int lane, uint32_t px[8])
+{
+    if (sizeof(T) == 1) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(row + lane * 8);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            px[k] = (v.x >> (8 * k)) & 0xffu;
+            px[k + 4] = (v.y >> (8 * k)) & 0xffu;
+        }
+    } else {
+        const uint4 v = *reinterpret_cast<const uint4 *>(row + lane * 8);
+        px[0] = v.x & 0xffffu; px[1] = v.x >> 16;
+        px[2] = v.y & 0xffffu; px[3] = v.y >> 16;
+        px[4] = v.z & 0xffffu; px[5] = v.z >> 16;
+        px[6] = v.w & 0xffffu; px[7] = v.w >> 16;
+    }
+}
+
+template <typename T, bool WQ, bool VEC, int TH>
+__global__ void __launch_bounds__(kWarps * 32, 1) k_onepass(OnePass a)
+{
+    using QA = typename QAcc<T>::type;
+    static_assert(TH == 32 || TH == 64, "rows per tile");
+    constexpr int RPL = TH / 32;                       // rows each lane keeps
+    constexpr int HREC = 2 * TH + 2;                   // horizontal record length
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *tile = reinterpret_cast<T *>(smem_raw) + (size_t)warp * TH * kSliceCols;
+    const int64_t ntiles = a.nby * a.nsx;
+
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(a.ticket, 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if ((int64_t)t >= ntiles || *(volatile uint32_t *)a.err) break;
+        if (t == 0 && a.stall_tile0) continue;
+        const int64_t b = t / a.nsx, s = t % a.nsx;
+        const int64_t y0 = b * TH;
+        const int nr = (int)min((int64_t)TH, a.rows - y0);
+        const int64_t x = s * kSliceCols + lane * kPxPerLane;
+
+        // Stage the tile (rows 0..nr-1; columns past the image read as 0).
+        for (int r = 0; r < nr; ++r) {
+            T *dst = tile + r * kSliceCols + lane * 8;
+            const T *src = reinterpret_cast<const T *>(a.img + (y0 + r) * a.pitch) + x;
+            if (VEC && x + 8 <= a.cols) {
+                if (sizeof(T) == 1) cp_async8(dst, src);
+                else cp_async16(dst, src);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) dst[k] = (x + k < a.cols) ? src[k] : (T)0;
+            }
+        }
+        cp_async_wait_all();
+        __syncwarp();
+
+        // Reduce: column sums (8 per lane), row sums (lane keeps rows lane + 32 j).
+        uint64_t cs[8], cq[8];
+        uint64_t rs_s[RPL], rs_q[RPL];
+        {
+            uint32_t c32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) { rs_s[j] = 0; rs_q[j] = 0; }
+            for (int r = 0; r < nr; ++r) {
+                uint32_t px[8];
+                smem8<T>(tile + r * kSliceCols, lane, px);
+                uint32_t rs = 0;
+                QA rq = 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    c32[k] += px[k];
+                    rs += px[k];
+                    if (WQ) {
+                        const QA p2 = (QA)px[k] * (QA)px[k];
+                        cqa[k] += p2;
+                        rq += p2;
+                    }
+                }
+                const uint64_t row_s = warp_sum(rs);
+                const uint64_t row_q = WQ ? (uint64_t)warp_sum(rq) : 0;
+                if ((r & 31) == lane) { rs_s[r >> 5] = row_s; rs_q[r >> 5] = row_q; }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { cs[k] = c32[k]; cq[k] = cqa[k]; }
+        }
+
+        // Vertical: publish the column sums, look back up the slice for V.
+        uint64_t vs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, vq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        {
+            uint64_t *ag = a.agg_v + (size_t)t * 512 + lane * 8;
+            uint64_t *in = a.inc_v + (size_t)t * 512 + lane * 8;
+            if (b > 0) {
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) {
+                    *reinterpret_cast<ulonglong2 *>(ag + k) = make_ulonglong2(cs[k], cs[k + 1]);
+                    if (WQ)
+                        *reinterpret_cast<ulonglong2 *>(ag + 256 + k) =
+                            make_ulonglong2(cq[k], cq[k + 1]);
+                }
+                publish(a.flag_v + t, kAgg);
+                bool ok = true;
+                for (int64_t bb = b - 1; bb >= 0; --bb) {
+                    const int64_t u = bb * a.nsx + s;
+                    const uint32_t f = wait_flag(a.flag_v + u, a.err);
+                    if (!f) { ok = false; break; }
+                    const uint64_t *src = (f == kInc ? a.inc_v : a.agg_v) + (size_t)u * 512 + lane * 8;
+#pragma unroll
+                    for (int k = 0; k < 8; k += 2) {
+                        const ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2 *>(src + k));
+                        vs[k] += w.x; vs[k + 1] += w.y;
+                        if (WQ) {
+                            const ulonglong2 z =
+                                __ldcg(reinterpret_cast<const ulonglong2 *>(src + 256 + k));
+                            vq[k] += z.x; vq[k + 1] += z.y;
+                        }
+                    }
+                    if (f == kInc) break;
+                }
+                if (!ok) break;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                *reinterpret_cast<ulonglong2 *>(in + k) =
+                    make_ulonglong2(vs[k] + cs[k], vs[k + 1] + cs[k + 1]);
+                if (WQ)
+                    *reinterpret_cast<ulonglong2 *>(in + 256 + k) =
+                        make_ulonglong2(vq[k] + cq[k], vq[k + 1] + cq[k + 1]);
+            }
+            publish(a.flag_v + t, kInc);
+        }
+
+        // Horizontal: own record = (row sums, total of V over the slice).
+        uint64_t vt_s = 0, vt_q = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { vt_s += vs[k]; vt_q += vq[k]; }
+        vt_s = warp_sum(vt_s);
+        if (WQ) vt_q = warp_sum(vt_q);
+        uint64_t lr_s[RPL], lr_q[RPL], K_s = 0, K_q = 0;
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) { lr_s[j] = 0; lr_q[j] = 0; }
+        {
+            uint64_t *ag = a.agg_h + (size_t)t * HREC;
+            uint64_t *in = a.inc_h + (size_t)t * HREC;
+            if (s > 0) {
+#pragma unroll
+                for (int j = 0; j < RPL; ++j) {
+                    ag[lane + 32 * j] = rs_s[j];
+                    if (WQ) ag[TH + lane + 32 * j] = rs_q[j];
+                }
+                if (lane == 0) { ag[2 * TH] = vt_s; ag[2 * TH + 1] = vt_q; }
+                publish(a.flag_h + t, kAgg);
+                bool ok = true;
+                for (int64_t ss = s - 1; ss >= 0; --ss) {
+                    const int64_t u = b * a.nsx + ss;
+                    const uint32_t f = wait_flag(a.flag_h + u, a.err);
+                    if (!f) { ok = false; break; }
+                    const uint64_t *src = (f == kInc ? a.inc_h : a.agg_h) + (size_t)u * HREC;
+#pragma unroll
+                    for (int j = 0; j < RPL; ++j) {
+                        lr_s[j] += __ldcg(src + lane + 32 * j);
+                        if (WQ) lr_q[j] += __ldcg(src + TH + lane + 32 * j);
+                    }
+                    K_s += __ldcg(src + 2 * TH);
+                    if (WQ) K_q += __ldcg(src + 2 * TH + 1);
+                    if (f == kInc) break;
+                }
+                if (!ok) break;
+            }
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                in[lane + 32 * j] = lr_s[j] + rs_s[j];
+                if (WQ) in[TH + lane + 32 * j] = lr_q[j] + rs_q[j];
+            }
+            if (lane == 0) { in[2 * TH] = K_s + vt_s; in[2 * TH + 1] = K_q + vt_q; }
+            publish(a.flag_h + t, kInc);
+        }
+
+        // Scan the staged tile: S = K + H[y] + V*[x] + lp.
+#pragma unroll
+        for (int k = 1; k < 8; ++k) { vs[k] += vs[k - 1]; if (WQ) vq[k] += vq[k - 1]; }
+        {
+            const uint64_t is = warp_incl_scan(vs[7], lane), es = is - vs[7];
+            const uint64_t iq = WQ ? warp_incl_scan(vq[7], lane) : 0, eq = iq - vq[7];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { vs[k] += es + K_s; if (WQ) vq[k] += eq + K_q; }
+        }
+        uint32_t cp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        uint64_t H_s = 0, H_q = 0;
+        for (int r = 0; r < nr; ++r) {
+            uint32_t px[8];
+            smem8<T>(tile + r * kSliceCols, lane, px);
+            uint64_t ls = lr_s[0], lq = lr_q[0];
+#pragma unroll
+            for (int j = 1; j < RPL; ++j)
+                if ((r >> 5) == j) { ls = lr_s[j]; lq = lr_q[j]; }
+            H_s += __shfl_sync(kFull, ls, r & 31);
+            if (WQ) H_q += __shfl_sync(kFull, lq, r & 31);
+            uint32_t lp[8];
+            QA lq8[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                cp[k] += px[k];
+                lp[k] = cp[k] + (k ? lp[k - 1] : 0u);
+                if (WQ) {
+                    cqa[k] += (QA)px[k] * (QA)px[k];
+                    lq8[k] = cqa[k] + (k ? lq8[k - 1] : (QA)0);
+                }
+            }
+            const int64_t y = y0 + r;
+            const uint32_t is = warp_incl_scan(lp[7], lane);
+            const uint64_t base_s = H_s + (uint64_t)(is - lp[7]);
+            uint64_t out[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) out[k] = base_s + vs[k] + lp[k];
+            store8(a.S + y * a.ld, x, a.cols, out);
+            if (WQ) {
+                const QA iq = warp_incl_scan(lq8[7], lane);
+                const uint64_t base_q = H_q + (uint64_t)(iq - lq8[7]);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) out[k] = base_q + vq[k] + (uint64_t)lq8[k];
+                store8(a.Q + y * a.ld, x, a.cols, out);
+            }
+        }
+        __syncwarp();     // the tile buffer is reused by the next ticket
+    }
+    cp_async_wait_all();
+}
+
+template <typename T> constexpr int onepass_rows() { return sizeof(T) == 1 ? 64 : 32; }
+
+template <typename T, bool WQ, bool VEC>
+swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
+                          char *scratch, uint32_t *err, cudaStream_t st)
+{
+    constexpr int TH = onepass_rows<T>();
+    OnePass a;
+    a.img = img;
+    a.pitch = p.pitch;
+    a.rows = p.rows;
+    a.cols = p.cols;
+    a.ld = p.ld;
+    a.nby = p.nby;
+    a.nsx = p.nsx;
+    a.S = S;
+    a.Q = Q;
+    a.err = err;
+    a.ticket = reinterpret_cast<uint32_t *>(scratch + p.off_ticket);
+    a.flag_v = reinterpret_cast<uint32_t *>(scratch + p.off_stat);
+    a.flag_h = a.flag_v + p.nby * p.nsx;
+    a.agg_v = reinterpret_cast<uint64_t *>(scratch + p.off_cs);
+    a.inc_v = a.agg_v + (size_t)p.nby * p.nsx * 512;
+    a.agg_h = reinterpret_cast<uint64_t *>(scratch + p.off_rs);
+    a.inc_h = a.agg_h + (size_t)p.nby * p.nsx * (2 * TH + 2);
+    a.stall_tile0 = (test_hooks() & SWA_HOOK_STALL_TILE0) ? 1u : 0u;
+    const size_t smem = (size_t)kWarps * TH * kSliceCols * sizeof(T);
+    auto kern = k_onepass<T, WQ, VEC, TH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) {
+        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t tiles = p.nby * p.nsx;
+    int64_t blocks = (int64_t)sms * per_sm;
+    const int64_t need = (tiles + kWarps - 1) / kWarps;
+    if (blocks > need) blocks = need;
+    if ((e = cudaMemsetAsync(scratch + p.off_ticket, 0, p.off_cs - p.off_ticket, st)) !=
+        cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    {
+        LaunchScope ls("sat_build", st);
+        kern<<<(unsigned)blocks, kWarps * 32, smem, st>>>(a);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("SAT build launch failed: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    return SWA_OK;
+}
+
+template <typename T>
+swa_status dispatch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
+                            char *scratch, uint32_t *err, cudaStream_t st)
+{
+    if (p.with_q)
+        return p.vec ? launch_onepass<T, true, true>(p, img, S, Q, scratch, err, st)
+                     : launch_onepass<T, true, false>(p, img, S, Q, scratch, err, st);
+    return p.vec ? launch_onepass<T, false, true>(p, img, S, Q, scratch, err, st)
+                 : launch_onepass<T, false, false>(p, img, S, Q, scratch, err, st);
+}
+
 int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
 
 }  // namespace
@@ -390,33 +790,52 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
     p.pitch = pitch;
     p.dtype = dtype;
     p.with_q = (flags & SWA_WITH_SQ) != 0;
-    p.twopass = true;
+    p.twopass = (flags & SWA_TWOPASS) != 0;
     p.ld = (cols + kLdAlign - 1) / kLdAlign * kLdAlign;
     p.vec = ((uintptr_t)image % 16 == 0) && (pitch % 16 == 0);
-    p.th = kTH;
-    p.nby = (rows + kTH - 1) / kTH;
+    p.th = p.twopass ? kTH : (dtype == SWA_U8 ? onepass_rows<uint8_t>()
+                                              : onepass_rows<uint16_t>());
+    p.nby = (rows + p.th - 1) / p.th;
     p.nsx = (cols + kSliceCols - 1) / kSliceCols;
     int64_t off = 0;
-    p.off_err = off;
-    off = align256(off + 16);
-    p.off_cs = off;
-    off = align256(off + 2 * p.nby * p.ld * 8);
-    p.off_rs = off;
-    off = align256(off + 2 * p.nsx * rows * 8);
-    p.off_bt = off;
-    off = align256(off + 4 * p.nby * p.nsx * 8);
-    p.off_stat = off;
-    p.off_ticket = off;
+    if (p.twopass) {
+        p.off_err = off;
+        off = align256(off + 16);
+        p.off_cs = off;
+        off = align256(off + 2 * p.nby * p.ld * 8);
+        p.off_rs = off;
+        off = align256(off + 2 * p.nsx * rows * 8);
+        p.off_bt = off;
+        off = align256(off + 4 * p.nby * p.nsx * 8);
+        p.off_stat = off;
+        p.off_ticket = off;
+    } else {
+        // ticket, then the two flag arrays (zeroed per build), then records.
+        const int64_t tiles = p.nby * p.nsx;
+        p.off_err = 0;
+        p.off_ticket = 0;
+        p.off_stat = 256;
+        off = align256(256 + 2 * tiles * 4);
+        p.off_cs = off;                                   // vertical records
+        off = align256(off + 2 * tiles * 512 * 8);
+        p.off_rs = off;                                   // horizontal records
+        off = align256(off + 2 * tiles * (2 * p.th + 2) * 8);
+        p.off_bt = off;
+    }
     p.scratch_bytes = off;
     return p;
 }
 
 swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S, uint64_t *Q,
-                        char *scratch, cudaStream_t st)
+                        char *scratch, uint32_t *err, cudaStream_t st)
 {
     const char *img = static_cast<const char *>(image);
-    if (p.dtype == SWA_U8) return dispatch_twopass<uint8_t>(p, img, S, Q, scratch, st);
-    return dispatch_twopass<uint16_t>(p, img, S, Q, scratch, st);
+    if (p.twopass) {
+        if (p.dtype == SWA_U8) return dispatch_twopass<uint8_t>(p, img, S, Q, scratch, st);
+        return dispatch_twopass<uint16_t>(p, img, S, Q, scratch, st);
+    }
+    if (p.dtype == SWA_U8) return dispatch_onepass<uint8_t>(p, img, S, Q, scratch, err, st);
+    return dispatch_onepass<uint16_t>(p, img, S, Q, scratch, err, st);
 }
 
 }  // namespace swa

@@ -25,6 +25,7 @@ bool g_pool_ready[kMaxDevices];
 std::atomic<int64_t> g_in_use[kMaxDevices];
 std::atomic<int64_t> g_limit{-1};
 std::atomic<int64_t> g_launches{0};
+std::atomic<uint32_t> g_hooks{0};
 std::unordered_set<Handle *> g_live;
 thread_local char t_err[512];
 
@@ -150,6 +151,8 @@ void set_error(const char *fmt, ...)
 }
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+uint32_t test_hooks() { return g_hooks.load(); }
 
 namespace {
 struct ProfRecord { const char *name; cudaEvent_t a, b; };
@@ -292,6 +295,13 @@ int32_t swa_profile_end(swa_kernel_time *out, int32_t max)
 
 int32_t swa_version(void) { return 10000; }
 
+swa_status swa_set_test_hooks(uint32_t hooks)
+{
+    if (hooks & ~(uint32_t)SWA_HOOK_STALL_TILE0) return SWA_EINVAL;
+    g_hooks.store(hooks);
+    return SWA_OK;
+}
+
 swa_status swa_window_shape(int64_t rows, int64_t cols, int64_t wh, int64_t ww, int64_t sy,
                             int64_t sx, int64_t *out_r, int64_t *out_c)
 {
@@ -400,7 +410,7 @@ swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols, int64_
     }
     if (dev_alloc(&mem, p.scratch_bytes, s, &st) != cudaSuccess) goto fail;
     scratch = static_cast<char *>(mem);
-    st = launch_build(p, d_image, h->S, h->Q, scratch, s);
+    st = launch_build(p, d_image, h->S, h->Q, scratch, h->d_err, s);
     dev_free(scratch, p.scratch_bytes, s);
     scratch = nullptr;
     if (st != SWA_OK) goto fail;

@@ -65,12 +65,13 @@ class LaunchScope {
     int slot_;
 };
 void set_error(const char *fmt, ...);
+uint32_t test_hooks();
 
 // SAT build (sat_build.cu).
 BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype,
                     uint32_t flags, const void *image);
 swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S,
-                        uint64_t *Q, char *scratch, cudaStream_t s);
+                        uint64_t *Q, char *scratch, uint32_t *err, cudaStream_t s);
 
 // Window statistics (window_stats.cu).
 struct WinDesc {

@@ -8,11 +8,16 @@
 //        exact because the true value is below 2^64), index -1 reading as 0;
 //   Qw likewise on Q;
 //   mean = Sw / n;  D = n*Qw - Sw^2 (exact, 128-bit);  std = sqrt(D) / n.
-// The 128-bit integer is rounded to double with a sticky bit (round to
-// nearest even), then the IEEE-rounded square root and divisions.
+// Both the integer path (exact_rn.cuh: the same roundings done in integer
+// arithmetic, used when n < 2^32) and the FP64 path (the 128-bit integer
+// rounded to double with a sticky bit, then the IEEE-rounded square root and
+// divisions) give the correctly rounded IEEE results of (double)Sw/(double)n
+// and sqrt((double)D)/(double)n, bit for bit.  The integer path exists
+// because GB300's FP64 divide and square root run at ~60 G/s per GPU.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "exact_rn.cuh"
 #include "swa_internal.h"
 
 namespace swa {
@@ -41,10 +46,11 @@ struct WinArgs {
     WinDesc w;
     double n_d;
     uint64_t n;
+    rn::Divisor div;      // n as an invariant divisor (integer path)
     int64_t nbx;          // blocks per output row
 };
 
-template <bool DO_SUM, bool DO_MEAN, bool DO_STD>
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN>
 __global__ void __launch_bounds__(256) k_windows(WinArgs a)
 {
     const int64_t i = blockIdx.x / a.nbx;
@@ -61,16 +67,21 @@ __global__ void __launch_bounds__(256) k_windows(WinArgs a)
     if (top && left) sw += __ldg(a.S + rt + x0 - 1);
     const int64_t o = i * a.w.out_ld + j;
     if (DO_SUM) a.w.sum[o] = sw;
-    if (DO_MEAN) a.w.mean[o] = __ddiv_rn(__ull2double_rn(sw), a.n_d);
+    if (DO_MEAN)
+        a.w.mean[o] = INT_RN ? rn::mean_rn(sw, a.div) : __ddiv_rn(__ull2double_rn(sw), a.n_d);
     if (DO_STD) {
         uint64_t qw = __ldg(a.Q + rb + x1);
         if (top) qw -= __ldg(a.Q + rt + x1);
         if (left) qw -= __ldg(a.Q + rb + x0 - 1);
         if (top && left) qw += __ldg(a.Q + rt + x0 - 1);
-        const unsigned __int128 D =
-            (unsigned __int128)a.n * qw - (unsigned __int128)sw * sw;
-        const double d = u128_to_double_rn((uint64_t)(D >> 64), (uint64_t)D);
-        a.w.std[o] = __ddiv_rn(__dsqrt_rn(d), a.n_d);
+        if (INT_RN) {
+            a.w.std[o] = rn::std_rn(a.n, sw, qw, a.div);
+        } else {
+            const unsigned __int128 D =
+                (unsigned __int128)a.n * qw - (unsigned __int128)sw * sw;
+            const double d = u128_to_double_rn((uint64_t)(D >> 64), (uint64_t)D);
+            a.w.std[o] = __ddiv_rn(__dsqrt_rn(d), a.n_d);
+        }
     }
 }
 
@@ -78,7 +89,10 @@ template <bool A, bool B, bool C>
 void launch_one(const WinArgs &a, unsigned blocks, cudaStream_t s)
 {
     LaunchScope ls("window_stats", s);
-    k_windows<A, B, C><<<blocks, 256, 0, s>>>(a);
+    if (a.n < (1ull << 32))
+        k_windows<A, B, C, true><<<blocks, 256, 0, s>>>(a);
+    else
+        k_windows<A, B, C, false><<<blocks, 256, 0, s>>>(a);
 }
 
 }  // namespace
@@ -94,6 +108,7 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
         a.w = w[k];
         a.n = (uint64_t)(w[k].wh * w[k].ww);
         a.n_d = (double)a.n;
+        a.div = rn::make_divisor(a.n < (1ull << 32) ? (uint32_t)a.n : 1u);
         a.nbx = (w[k].C + 255) / 256;
         const int64_t blocks = a.nbx * w[k].R;
         if (blocks <= 0) continue;

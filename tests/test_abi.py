@@ -104,3 +104,8 @@ def test_sat_bytes(L):
     ld = (85000 + 31) // 32 * 32
     assert t.value == 2 * 8 * 70000 * ld
     assert s.value < t.value // 16
+
+
+def test_test_hooks_validate(L):
+    assert L.swa_set_test_hooks(0) == swa.SWA_OK
+    assert L.swa_set_test_hooks(2) == swa.SWA_EINVAL

@@ -1,0 +1,114 @@
+"""The CUDA path's integer round-to-nearest helpers (exact_rn.cuh), built for
+the host and compared bit for bit with the oracle's IEEE double arithmetic
+(CPU only).  The same code runs in the window kernel on the GPU."""
+import ctypes
+import math
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rn():
+    out = os.path.join(tempfile.mkdtemp(), "exact_rn_host.so")
+    subprocess.check_call([
+        "g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+        "-I", os.path.join(ROOT, "paper_2410_16291_gb300", "csrc"),
+        os.path.join(ROOT, "tests", "exact_rn_host.cpp"), "-o", out])
+    L = ctypes.CDLL(out)
+    vp = ctypes.c_void_p
+    L.rn_stats_bulk.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp]
+    L.rn_u128.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    L.rn_u128.restype = ctypes.c_double
+    L.rn_sqrt.argtypes = [ctypes.c_double]
+    L.rn_sqrt.restype = ctypes.c_double
+    L.rn_div.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
+    L.rn_div.restype = ctypes.c_double
+    return L
+
+
+def run_bulk(rn, n, sw, qw):
+    n, sw, qw = (np.ascontiguousarray(a, dtype=np.uint64) for a in (n, sw, qw))
+    m = np.empty(len(n))
+    s = np.empty(len(n))
+    rn.rn_stats_bulk(n.ctypes.data, sw.ctypes.data, qw.ctypes.data, len(n), m.ctypes.data,
+                     s.ctypes.data)
+    return m, s
+
+
+def moments(rng, count, nmax, vmax):
+    """Random valid (n, Sw, Qw): Qw in [ceil(Sw^2/n), Sw*vmax]."""
+    n = rng.integers(1, nmax + 1, count, dtype=np.uint64)
+    sw = (rng.random(count) * n.astype(float) * vmax).astype(np.uint64)
+    lo = np.array([-(-int(a) * int(a) // int(b)) for a, b in zip(sw, n)], dtype=object)
+    hi = np.array([max(int(a) * vmax, l) for a, l in zip(sw, lo)], dtype=object)
+    f = rng.random(count)
+    qw = np.array([int(l + (h - l) * x) for l, h, x in zip(lo, hi, f)], dtype=np.uint64)
+    return n, sw, qw
+
+
+@pytest.mark.parametrize("nmax,vmax", [(1024 ** 2, 255), (1024 ** 2, 65535), (2 ** 32 - 1, 255),
+                                       (2 ** 32 - 1, 65535), (64, 65535), (4, 3)])
+def test_stats_bitexact_random(rn, nmax, vmax):
+    rng = np.random.default_rng(nmax ^ vmax)
+    n, sw, qw = moments(rng, 20000, nmax, vmax)
+    m0, s0 = oracle.stats_bulk(n, sw, qw)
+    m1, s1 = run_bulk(rn, n, sw, qw)
+    np.testing.assert_array_equal(m1, m0)
+    np.testing.assert_array_equal(s1, s0)
+
+
+def test_stats_window_areas_and_edges(rn):
+    """Square windows of every side 1..1024 with constant, two-valued and
+    extreme moments."""
+    ns, sws, qws = [], [], []
+    for w in range(1, 1025):
+        n = w * w
+        for v in (0, 1, 255, 65535):
+            ns.append(n); sws.append(n * v); qws.append(n * v * v)          # constant: D = 0
+        for k in (1, n // 3, n // 2, n - 1):
+            if 0 < k < n:                                                      # k of 65535, rest 0
+                ns.append(n); sws.append(k * 65535); qws.append(k * 65535 ** 2)
+                ns.append(n); sws.append(k * 255 + (n - k)); qws.append(k * 255 ** 2 + (n - k))
+    m0, s0 = oracle.stats_bulk(ns, sws, qws)
+    m1, s1 = run_bulk(rn, ns, sws, qws)
+    np.testing.assert_array_equal(m1, m0)
+    np.testing.assert_array_equal(s1, s0)
+
+
+def test_u128_rounding_ties_to_even(rn):
+    vals = [1, 2**53 - 1, 2**53 + 1, 2**53 + 3, 2**54 + 2, 2**54 + 6, 2**64 - 1, 2**64 + 2**11,
+            2**64 + 3 * 2**11, 2**64 + 2**11 + 1, 2**100 + 2**47, 2**100 + 3 * 2**47,
+            2**127 + 2**74, 2**127 + 2**74 + 1, 2**128 - 1]
+    rng = np.random.default_rng(3)
+    for _ in range(20000):
+        b = int(rng.integers(1, 128))
+        vals.append(int.from_bytes(rng.bytes(16), "little") >> (128 - b))
+    for v in vals:
+        assert rn.rn_u128(v >> 64, v & (2**64 - 1)) == float(v), v
+
+
+def test_sqrt_correctly_rounded(rn):
+    rng = np.random.default_rng(11)
+    xs = list(rng.random(20000) * 2.0 ** rng.integers(-60, 120, 20000))
+    xs += [float(k * k) for k in range(1, 3000)] + [float(k * k + 1) for k in range(1, 3000)]
+    xs += [2.0 ** e for e in range(-60, 120)] + [math.nextafter(2.0 ** e, 0) for e in range(-50, 100)]
+    for x in xs:
+        if x > 0:
+            assert rn.rn_sqrt(x) == math.sqrt(x), x
+
+
+def test_division_correctly_rounded(rn):
+    rng = np.random.default_rng(12)
+    for _ in range(30000):
+        n = int(rng.integers(1, 2**32))
+        a = int(rng.integers(0, 2**63)) >> int(rng.integers(0, 63))
+        want = float(a) / float(n)
+        assert rn.rn_div(a, n) == want, (a, n)
