@@ -85,13 +85,48 @@ SWA_HD float approx_rsqrt(float x)
 #endif
 }
 
-SWA_HD int64_t round_to_i64(float x)
+// float estimate of a signed 64-bit integer.  On the device the conversion
+// instruction is used (it issues to the FP64 pipe, which this code otherwise
+// leaves idle, while the integer work keeps the ALU pipe busy); the host
+// version truncates to 24 bits with integer operations.
+SWA_HD float i64_to_float_trunc(int64_t v)
 {
 #if defined(__CUDA_ARCH__)
-    return __float2ll_rn(x);
-#else
-    return llrintf(x);
+    return __ll2float_rz(v);
 #endif
+    if (v == 0) return 0.0f;
+    const uint32_t sign = v < 0 ? 0x80000000u : 0u;
+    const uint64_t mag = v < 0 ? (uint64_t)0 - (uint64_t)v : (uint64_t)v;
+    const int lz = clz64(mag);
+    const uint64_t m = mag << lz;                       // top bit at 63
+    return bits_to_float(sign | ((uint32_t)(127 + 63 - lz) << 23) |
+                         ((uint32_t)(m >> 40) & 0x7fffffu));
+}
+
+SWA_HD uint32_t float_bits(float f)
+{
+#if defined(__CUDA_ARCH__)
+    return __float_as_uint(f);
+#else
+    uint32_t b;
+    __builtin_memcpy(&b, &f, 4);
+    return b;
+#endif
+}
+
+// Signed 64-bit integer from a float with |x| < 2^62, truncating toward zero
+// (the conversion instruction on the device, integer operations on the host).
+SWA_HD int64_t float_to_i64_trunc(float x)
+{
+#if defined(__CUDA_ARCH__)
+    return __float2ll_rz(x);
+#endif
+    const uint32_t b = float_bits(x);
+    const int e = (int)((b >> 23) & 0xffu) - 127;
+    if (e < 0) return 0;
+    const uint64_t m = (b & 0x7fffffu) | 0x800000u;
+    const uint64_t mag = e >= 23 ? m << (e - 23) : m >> (23 - e);
+    return (b >> 31) ? -(int64_t)mag : (int64_t)mag;
 }
 
 // A value sig * 2^exp with sig < 2^53 (sig == 0 means zero).
@@ -141,9 +176,11 @@ SWA_HD Fp round_u128(uint64_t hi, uint64_t lo)
 
 // Divisor n in [1, 2^32): normalized d = n << z (top bit set) and
 // v = floor((2^64 - 1) / d) - 2^32.
+// pow2: n is a power of two, so a/n is exact (an exponent shift by 31 - z).
 struct Divisor {
     uint32_t d, v;
     int z;
+    int pow2;
 };
 
 static inline Divisor make_divisor(uint32_t n)
@@ -152,6 +189,7 @@ static inline Divisor make_divisor(uint32_t n)
     D.z = n ? __builtin_clz(n) : 0;
     D.d = n << D.z;
     D.v = (uint32_t)(0xffffffffffffffffull / D.d - (1ull << 32));
+    D.pow2 = n && (n & (n - 1)) == 0;
     return D;
 }
 
@@ -173,6 +211,11 @@ SWA_HD uint64_t div_rn(uint64_t a, int aexp, const Divisor &D)
 {
     if (a == 0) return 0;
     const int la = 64 - clz64(a);
+    if (D.pow2) {                                  // exact: a * 2^(aexp - log2 n)
+        const uint64_t M = a << (53 - la);         // [2^52, 2^53)
+        const int E = la - 1 + aexp - (31 - D.z);
+        return ((uint64_t)(E + 1023) << 52) | (M & ((1ull << 52) - 1));
+    }
     const int s = 86 - la;                         // a << s has 86 bits
     uint64_t hi, lo;
     if (s >= 64) { hi = a << (s - 64); lo = 0; }
@@ -209,6 +252,15 @@ SWA_HD void residual(uint64_t Nhi, uint64_t Nlo, uint64_t R, int64_t *rhi, uint6
 }
 
 // RN(sqrt(sig * 2^exp)) for 1 <= sig < 2^53.
+//
+// Error budget: the seed R0 = fx * rsqrt(fx) * 2^26 has relative error below
+// 2^-21 (24-bit truncation of Mx, rsqrtf within 2 ulp, two float roundings),
+// so |R0 - sqrt(N)| < 2^32.  A correction R += (N - R^2) / (2R), with the
+// quotient formed in FP32 from the exact residual, leaves |R1 - sqrt(N)| <
+// 2^12 (2^11 from the quotient's 2^-21 relative error, 2^11 from Newton's
+// quadratic term), and a second one leaves |R2 - sqrt(N)| < 1.01 including
+// the truncation to an integer, so R2 is within -1..+2 of floor(sqrt(N)):
+// two exact steps each way (updating the remainder arithmetically) reach it.
 SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
 {
     const int L = 64 - clz64(sig);
@@ -221,8 +273,7 @@ SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
     const float fx = bits_to_float(((uint32_t)(LM - 1 + 127) << 23) |
                                    ((uint32_t)(Mx >> (LM - 24)) & 0x7fffffu));
     const float y = approx_rsqrt(fx);
-    uint64_t R = (uint64_t)round_to_i64(fx * y * 67108864.0f);    // 2^26
-    // Two Newton corrections R += (N - R^2) / (2R), the quotient from FP32.
+    uint64_t R = (uint64_t)float_to_i64_trunc(fx * y * 67108864.0f);   // 2^26
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
         int64_t rh;
@@ -230,31 +281,22 @@ SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
         residual(Nhi, Nlo, R, &rh, &rl);
         // (rh:rl) >> 32 fits int64 (|N - R^2| < 2^95)
         const int64_t top = (int64_t)(((uint64_t)rh << 32) | (rl >> 32));
-        const float dlt = (float)top * y * 32.0f;   // * 2^32 / 2^27
-        R = (uint64_t)((int64_t)R + round_to_i64(dlt));
+        const float dlt = i64_to_float_trunc(top) * y * 32.0f;   // * 2^32 / 2^27
+        R = (uint64_t)((int64_t)R + float_to_i64_trunc(dlt));
     }
-    // Exact floor: 0 <= N - R^2 <= 2R.
+    // Exact floor: 0 <= rem = N - R^2 <= 2R.  rem is within (-2^57, 2^57).
     int64_t rh;
     uint64_t rl;
     residual(Nhi, Nlo, R, &rh, &rl);
+    int64_t rem = (int64_t)rl;                     // rh is its sign extension
 #pragma unroll
-    for (int it = 0; it < 3; ++it) {
-        if (rh < 0) {                              // R too large
-            --R;
-            residual(Nhi, Nlo, R, &rh, &rl);
-        }
-    }
+    for (int it = 0; it < 2; ++it)
+        if (rem < 0) { --R; rem += (int64_t)(2 * R + 1); }
 #pragma unroll
-    for (int it = 0; it < 3; ++it) {
-        // rem > 2R  <=>  R too small
-        const uint64_t twoR = 2 * R;
-        if (rh > 0 || (rh == 0 && rl > twoR)) {
-            ++R;
-            residual(Nhi, Nlo, R, &rh, &rl);
-        }
-    }
-    // Round to nearest: up iff rem > R (rem <= 2R < 2^55, so rh == 0).
-    R += (rh == 0 && rl > R) ? 1u : 0u;
+    for (int it = 0; it < 2; ++it)
+        if (rem > (int64_t)(2 * R)) { rem -= (int64_t)(2 * R + 1); ++R; }
+    // Round to nearest: up iff rem > R.
+    R += rem > (int64_t)R ? 1u : 0u;
     int e = E / 2 - 26;
     if (R >> 53) { R >>= 1; ++e; }
     return Fp{R, e};

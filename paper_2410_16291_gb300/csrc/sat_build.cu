@@ -20,8 +20,12 @@
 // kernel turns them into exclusive scans; the scan kernel re-reads the image
 // and writes S (and Q, the same for I^2).  Table entries are exact uint64;
 // tile-local parts use 32-bit integers where their bounds allow.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "swa_internal.h"
 
@@ -36,34 +40,47 @@ constexpr int kWarps = 8;                 // warps per block in tile kernels
 template <typename T> struct QAcc { using type = uint32_t; };
 template <> struct QAcc<uint16_t> { using type = uint64_t; };
 
-// Load 8 consecutive pixels of row y starting at column x; pixels at or past
-// `cols` read as 0.  VEC: the image base and pitch are 16-byte aligned, so a
-// full chunk is one 8- or 16-byte load.
+// Load 8 consecutive pixels of row y starting at column x, packed (2 words
+// for uint8, 4 for uint16) until used; pixels at or past `cols` read as 0.
+// VEC: the image base and pitch are aligned to 8 pixels' bytes, so a full
+// chunk is one 8- (uint8) or 16-byte (uint16) load.
+template <typename T> struct Raw8 { uint32_t w[sizeof(T) * 2]; };
+
 template <typename T, bool VEC>
-__device__ __forceinline__ void load8(const char *__restrict__ img, int64_t pitch,
-                                      int64_t y, int64_t x, int64_t cols,
-                                      uint32_t px[8])
+__device__ __forceinline__ Raw8<T> load_raw8(const char *__restrict__ img, int64_t pitch,
+                                             int64_t y, int64_t x, int64_t cols)
 {
+    Raw8<T> r;
     const T *row = reinterpret_cast<const T *>(img + y * pitch);
     if (VEC && x + 8 <= cols) {
         if (sizeof(T) == 1) {
-            uint2 v = __ldg(reinterpret_cast<const uint2 *>(row + x));
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                px[k] = (v.x >> (8 * k)) & 0xffu;
-                px[k + 4] = (v.y >> (8 * k)) & 0xffu;
-            }
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(row + x));
+            r.w[0] = v.x; r.w[1] = v.y;
         } else {
-            uint4 v = __ldg(reinterpret_cast<const uint4 *>(row + x));
-            px[0] = v.x & 0xffffu; px[1] = v.x >> 16;
-            px[2] = v.y & 0xffffu; px[3] = v.y >> 16;
-            px[4] = v.z & 0xffffu; px[5] = v.z >> 16;
-            px[6] = v.w & 0xffffu; px[7] = v.w >> 16;
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row + x));
+            r.w[0] = v.x; r.w[1] = v.y; r.w[2 % (sizeof(T) * 2)] = v.z;
+            r.w[3 % (sizeof(T) * 2)] = v.w;
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            px[k] = (x + k < cols) ? (uint32_t)__ldg(row + x + k) : 0u;
+        for (int i = 0; i < (int)sizeof(T) * 2; ++i) r.w[i] = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t v = (x + k < cols) ? (uint32_t)__ldg(row + x + k) : 0u;
+            if (sizeof(T) == 1) r.w[k >> 2] |= v << (8 * (k & 3));
+            else r.w[(k >> 1) % (sizeof(T) * 2)] |= v << (16 * (k & 1));
+        }
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void unpack8(const Raw8<T> &r, uint32_t px[8])
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (sizeof(T) == 1) px[k] = (r.w[k >> 2] >> (8 * (k & 3))) & 0xffu;
+        else px[k] = (r.w[(k >> 1) % (sizeof(T) * 2)] >> (16 * (k & 1))) & 0xffffu;
     }
 }
 
@@ -86,19 +103,23 @@ __device__ __forceinline__ uint64_t warp_sum(uint64_t v)
     return v;
 }
 
-// Store 8 consecutive table entries of one row (16-byte vector stores when
-// the whole chunk is inside the row).
-__device__ __forceinline__ void store8(uint64_t *__restrict__ dst, int64_t x, int64_t cols,
-                                       const uint64_t v[8])
+// The lane's 8 consecutive staged pixels of one row.
+template <typename T>
+__device__ __forceinline__ void smem8(const T *row, int lane, uint32_t px[8])
 {
-    if (x + 8 <= cols) {
-        ulonglong2 *d = reinterpret_cast<ulonglong2 *>(dst + x);
+    if (sizeof(T) == 1) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(row + lane * 8);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) d[k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
+        for (int k = 0; k < 4; ++k) {
+            px[k] = (v.x >> (8 * k)) & 0xffu;
+            px[k + 4] = (v.y >> (8 * k)) & 0xffu;
+        }
     } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (x + k < cols) dst[x + k] = v[k];
+        const uint4 v = *reinterpret_cast<const uint4 *>(row + lane * 8);
+        px[0] = v.x & 0xffffu; px[1] = v.x >> 16;
+        px[2] = v.y & 0xffffu; px[3] = v.y >> 16;
+        px[4] = v.z & 0xffffu; px[5] = v.z >> 16;
+        px[6] = v.w & 0xffffu; px[7] = v.w >> 16;
     }
 }
 
@@ -129,9 +150,18 @@ k_reduce(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols
     uint32_t cs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     QA cq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint64_t keep_s = 0, keep_q = 0, tot_s = 0, tot_q = 0;
-    uint32_t px[8];
-    for (int64_t y = y0; y < y1; ++y) {
-        load8<T, VEC>(img, pitch, y, x, cols, px);
+    constexpr int PF = 8;
+    for (int64_t ya = y0; ya < y1; ya += PF) {
+      Raw8<T> raw[PF];
+#pragma unroll
+      for (int i = 0; i < PF; ++i)
+          if (ya + i < y1) raw[i] = load_raw8<T, VEC>(img, pitch, ya + i, x, cols);
+#pragma unroll
+      for (int i = 0; i < PF; ++i) {
+        const int64_t y = ya + i;
+        if (y >= y1) break;
+        uint32_t px[8];
+        unpack8<T>(raw[i], px);
         uint32_t rs = 0;
         QA rq = 0;
 #pragma unroll
@@ -157,6 +187,7 @@ k_reduce(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols
                 if (WQ) c.rs_q[s * rows + yy] = keep_q;
             }
         }
+      }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -236,22 +267,131 @@ k_carry(int64_t rows, int64_t cols, int64_t ld, int64_t nby, int64_t nsx,
     }
 }
 
+// ------------------------------------------------------ TMA row output --
+// Rows of S and Q leave through shared memory by TMA tensor stores
+// (cp.async.bulk.tensor) from a two-slot ring per warp.  The ring holds each
+// 2 KB row segment (256 uint64) as 16 "rows" of 128 bytes in the 128-byte
+// swizzled layout the tensor map declares; with lane l owning columns
+// 8l..8l+7 that layout makes the warp's 16-byte shared stores free of bank
+// conflicts.  The bulk stores do not occupy the load/store unit, carry an
+// L2 evict-first hint (the tables stream out at 16 bytes per pixel and are
+// not re-read soon), and are not waited for by generic-proxy memory fences.
+constexpr int kRing = 2;                           // output row slots per warp
+constexpr int kRowBytes = kSliceCols * 8;          // one table row segment (2 KB)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// TMA tensor store of one 16 x 16 box of uint64 (a 256-column row segment)
+// at coordinates (0, x0/16, y), in the current bulk group.
+__device__ __forceinline__ void tma_store_row_hint(const CUtensorMap *tm, const void *smem,
+                                                   int c1, int c2, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group.L2::cache_hint"
+        " [%0, {%1, %2, %3}], [%4], %5;" ::"l"(reinterpret_cast<uint64_t>(tm)),
+        "r"(0), "r"(c1), "r"(c2), "r"(smem_addr(smem)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit()
+{
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Wait until at most kRing-1 bulk groups still read their shared source.
+__device__ __forceinline__ void bulk_wait_ring()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kRing - 1) : "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all()
+{
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Byte offset, inside a 1024-aligned 2 KB row buffer in the tensor map's
+// 128-byte swizzle, of the 16-byte chunk j (elements 8l+2j, 8l+2j+1) of lane
+// l: box row l/2, chunk (4(l%2) + j) XOR (row mod 8).
+__device__ __forceinline__ int swz_off(int lane, int j)
+{
+    const int r = lane >> 1;
+    return r * 128 + ((((lane & 1) << 2) + j) ^ (r & 7)) * 16;
+}
+
+// One output row: the warp writes its 8 S (and Q) values per lane into the
+// ring slot, then lane 0 issues the tensor stores.  Values are
+// base + pre[k] + lp[k] (uint64 + uint64 + tile-local partial).
+template <bool WQ, typename QA>
+__device__ __forceinline__ void emit_row(unsigned char *ring, int &slot, const int sw[4],
+                                         uint64_t base_s, const uint64_t vs[8],
+                                         const uint32_t lp[8], uint64_t base_q,
+                                         const uint64_t vq[8], const QA lq[8],
+                                         const CUtensorMap *tmS, const CUtensorMap *tmQ,
+                                         int c1, int y, uint64_t pol)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned char *rs = ring + slot * (2 * kRowBytes);
+    unsigned char *rq = rs + kRowBytes;
+    if (lane == 0) bulk_wait_ring();     // the slot's previous copy has read it
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<ulonglong2 *>(rs + sw[j]) =
+            make_ulonglong2(base_s + vs[2 * j] + lp[2 * j], base_s + vs[2 * j + 1] + lp[2 * j + 1]);
+    if (WQ) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<ulonglong2 *>(rq + sw[j]) =
+                make_ulonglong2(base_q + vq[2 * j] + (uint64_t)lq[2 * j],
+                                base_q + vq[2 * j + 1] + (uint64_t)lq[2 * j + 1]);
+    }
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        tma_store_row_hint(tmS, rs, c1, y, pol);
+        if (WQ) tma_store_row_hint(tmQ, rq, c1, y, pol);
+        bulk_commit();
+    }
+    slot = (slot + 1) % kRing;
+}
+
 // ------------------------------------------------------------------ scan --
-// One warp per tile: assemble the carries, then walk the tile's rows keeping
-// per-column running sums, scan each row across the warp and store S (and Q).
+// Two-pass build, second pass: one warp per tile; assemble the carries, then
+// walk the tile's rows keeping per-column running sums, scan each row across
+// the warp and write S (and Q) through the ring.
 template <typename T, bool WQ, bool VEC, int TH>
 __global__ void __launch_bounds__(kWarps * 32)
 k_scan(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
-       int64_t ld, int64_t nby, int64_t nsx, Carries c, uint64_t *__restrict__ S,
-       uint64_t *__restrict__ Q)
+       int64_t ld, int64_t nby, int64_t nsx, Carries c,
+       const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmQ)
 {
     using QA = typename QAcc<T>::type;
-    const int lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    constexpr int RING_BYTES = kRing * 2 * kRowBytes;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    unsigned char *ring = base + (size_t)warp * RING_BYTES;
+    const int64_t t = (int64_t)blockIdx.x * kWarps + warp;
     if (t >= nby * nsx) return;
     const int64_t b = t / nsx, s = t % nsx;
     const int64_t y0 = b * TH, y1 = min(rows, y0 + TH);
     const int64_t x = s * kSliceCols + lane * kPxPerLane;
+    const uint64_t pol = l2_evict_first_policy();
 
     // K: exclusive 2-D sum of tile totals above-left = sum over bands < b of
     // the (already slice-scanned) totals.
@@ -280,15 +420,21 @@ k_scan(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
         for (int k = 0; k < 8; ++k) { vs[k] += es + K_s; if (WQ) vq[k] += eq + K_q; }
     }
 
+    int sw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sw[j] = swz_off(lane, j);
+    const int c1 = (int)(s * (kSliceCols / 16));
+    int slot = 0;
     uint32_t cp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     QA cq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint64_t H_s = 0, H_q = 0, lr_s = 0, lr_q = 0;
-    uint32_t px[8], nx[8];
-    if (y0 < y1) load8<T, VEC>(img, pitch, y0, x, cols, nx);
+    Raw8<T> pa = load_raw8<T, VEC>(img, pitch, y0, x, cols), pb = pa;
+    if (y0 + 1 < y1) pb = load_raw8<T, VEC>(img, pitch, y0 + 1, x, cols);
     for (int64_t y = y0; y < y1; ++y) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) px[k] = nx[k];
-        if (y + 1 < y1) load8<T, VEC>(img, pitch, y + 1, x, cols, nx);
+        uint32_t px[8];
+        unpack8<T>(pa, px);
+        pa = pb;
+        if (y + 2 < y1) pb = load_raw8<T, VEC>(img, pitch, y + 2, x, cols);
         const int r = (int)(y - y0) & 31;
         if (r == 0) {
             const int64_t yy = y + lane;
@@ -311,73 +457,17 @@ k_scan(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
         }
         const uint32_t is = warp_incl_scan(lp[7], lane);
         const uint64_t base_s = H_s + (uint64_t)(is - lp[7]);
-        uint64_t out[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) out[k] = base_s + vs[k] + lp[k];
-        store8(S + y * ld, x, cols, out);
+        uint64_t base_q = 0;
         if (WQ) {
             const QA iq = warp_incl_scan(lq[7], lane);
-            const uint64_t base_q = H_q + (uint64_t)(iq - lq[7]);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) out[k] = base_q + vq[k] + (uint64_t)lq[k];
-            store8(Q + y * ld, x, cols, out);
+            base_q = H_q + (uint64_t)(iq - lq[7]);
         }
+        emit_row<WQ, QA>(ring, slot, sw, base_s, vs, lp, base_q, vq, lq, &tmS, &tmQ, c1, (int)y,
+                         pol);
     }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
 }
-
-constexpr int kTH = 128;   // rows per tile (u8 tile-local Q sums stay below 2^32)
-
-template <typename T, bool WQ, bool VEC>
-swa_status launch_twopass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
-                          char *scratch, cudaStream_t st)
-{
-    Carries c;
-    const int64_t nb = p.nby, ns = p.nsx;
-    c.cs_s = reinterpret_cast<uint64_t *>(scratch + p.off_cs);
-    c.cs_q = c.cs_s + nb * p.ld;
-    c.rs_s = reinterpret_cast<uint64_t *>(scratch + p.off_rs);
-    c.rs_q = c.rs_s + ns * p.rows;
-    c.tt_s = reinterpret_cast<uint64_t *>(scratch + p.off_bt);
-    c.tt_q = c.tt_s + nb * ns;
-    c.tk_s = c.tt_q + nb * ns;
-    c.tk_q = c.tk_s + nb * ns;
-    const int64_t tiles = nb * ns;
-    const int64_t blocks = (tiles + kWarps - 1) / kWarps;
-    {
-        LaunchScope ls("sat_reduce", st);
-        k_reduce<T, WQ, VEC, kTH><<<(unsigned)blocks, kWarps * 32, 0, st>>>(
-            img, p.pitch, p.rows, p.cols, p.ld, nb, ns, c);
-    }
-    const int64_t nA = (p.cols + 255) / 256, nB = (p.rows + 255) / 256, nC = (nb + 255) / 256;
-    {
-        LaunchScope ls("sat_carry", st);
-        k_carry<WQ><<<(unsigned)(nA + nB + nC), 256, 0, st>>>(p.rows, p.cols, p.ld, nb, ns,
-                                                              nA, nB, c);
-    }
-    {
-        LaunchScope ls("sat_scan", st);
-        k_scan<T, WQ, VEC, kTH><<<(unsigned)blocks, kWarps * 32, 0, st>>>(
-            img, p.pitch, p.rows, p.cols, p.ld, nb, ns, c, S, Q);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        set_error("SAT build launch failed: %s", cudaGetErrorString(e));
-        return SWA_ECUDA;
-    }
-    return SWA_OK;
-}
-
-template <typename T>
-swa_status dispatch_twopass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
-                            char *scratch, cudaStream_t st)
-{
-    if (p.with_q)
-        return p.vec ? launch_twopass<T, true, true>(p, img, S, Q, scratch, st)
-                     : launch_twopass<T, true, false>(p, img, S, Q, scratch, st);
-    return p.vec ? launch_twopass<T, false, true>(p, img, S, Q, scratch, st)
-                 : launch_twopass<T, false, false>(p, img, S, Q, scratch, st);
-}
-
 
 // ------------------------------------------------------------- one pass --
 // Single-pass build with decoupled look-back.  Warps take tiles in row-major
@@ -390,17 +480,18 @@ swa_status dispatch_twopass(const BuildPlan &p, const char *img, uint64_t *S, ui
 //              right).
 // It then looks back up its slice for the column carries V (summing
 // aggregates until a tile with an inclusive prefix is found), publishes its
-// own inclusive column prefix, looks back left along its band for the row
-// carries LR and K the same way, publishes its inclusive row prefix, and
-// finally scans the staged tile and writes S and Q.  Every wait is bounded by
-// a time limit; on expiry the warp sets the error word and all warps stop.
+// own inclusive column prefix together with its horizontal aggregate, looks
+// back left along its band for the row carries LR and K the same way,
+// publishes its inclusive row prefix, and finally scans the staged tile and
+// writes S and Q through the ring.  Every wait is bounded by a time limit; on
+// expiry the warp sets the error word and all warps stop.
 constexpr uint32_t kAgg = 1u, kInc = 2u;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
+constexpr int kOpWarps = 8;                        // warps per block (independent tiles)
 
 struct OnePass {
     const char *img;
     int64_t pitch, rows, cols, ld, nby, nsx;
-    uint64_t *S, *Q;
     uint32_t *ticket, *err;
     uint32_t *flag_v, *flag_h;        // [tiles]
     uint64_t *agg_v, *inc_v;          // [tiles][2][256]
@@ -415,9 +506,9 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
     return v;
 }
 
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ uint64_t global_ns()
@@ -449,24 +540,29 @@ __device__ __noinline__ uint32_t wait_flag(const uint32_t *flag, uint32_t *err)
     }
 }
 
-// Every lane has written its part of a record; make it visible, then flag it.
-__device__ __forceinline__ void publish(uint32_t *flag, uint32_t v)
+// Every lane has written its part of the records; make them visible, then
+// raise up to two flags (a fence followed by relaxed stores is a release).
+__device__ __forceinline__ void publish(uint32_t *f1, uint32_t v1, uint32_t *f2 = nullptr,
+                                        uint32_t v2 = 0)
 {
     __threadfence();
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) st_release(flag, v);
+    if ((threadIdx.x & 31) == 0) {
+        st_relaxed(f1, v1);
+        if (f2) st_relaxed(f2, v2);
+    }
 }
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *g)
 {
-    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(g)
+                 : "memory");
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *g)
 {
-    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(g) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(g)
+                 : "memory");
 }
 
 __device__ __forceinline__ void cp_async_wait_all()
@@ -474,37 +570,30 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// Unpack the 8 staged pixels of one lane for one row.
-template <typename T>
-__device__ __forceinline__ void smem8(const T *row, int lane, uint32_t px[8])
-{
-    if (sizeof(T) == 1) {
-        const uint2 v = *reinterpret_cast<const uint2 *>(row + lane * 8);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            px[k] = (v.x >> (8 * k)) & 0xffu;
-            px[k + 4] = (v.y >> (8 * k)) & 0xffu;
-        }
-    } else {
-        const uint4 v = *reinterpret_cast<const uint4 *>(row + lane * 8);
-        px[0] = v.x & 0xffffu; px[1] = v.x >> 16;
-        px[2] = v.y & 0xffffu; px[3] = v.y >> 16;
-        px[4] = v.z & 0xffffu; px[5] = v.z >> 16;
-        px[6] = v.w & 0xffffu; px[7] = v.w >> 16;
-    }
-}
-
 template <typename T, bool WQ, bool VEC, int TH>
-__global__ void __launch_bounds__(kWarps * 32, 1) k_onepass(OnePass a)
+__global__ void __launch_bounds__(kOpWarps * 32, 1)
+k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
+          const __grid_constant__ CUtensorMap tmQ)
 {
     using QA = typename QAcc<T>::type;
     static_assert(TH == 32 || TH == 64, "rows per tile");
     constexpr int RPL = TH / 32;                       // rows each lane keeps
     constexpr int HREC = 2 * TH + 2;                   // horizontal record length
+    constexpr int TILE_BYTES = TH * kSliceCols * (int)sizeof(T);
+    constexpr int RING_BYTES = kRing * 2 * kRowBytes;
+    constexpr int WARP_BYTES = RING_BYTES + TILE_BYTES;
+    static_assert(WARP_BYTES % 1024 == 0, "ring slots stay 1024-byte aligned");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T *tile = reinterpret_cast<T *>(smem_raw) + (size_t)warp * TH * kSliceCols;
+    unsigned char *base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    unsigned char *ring = base + (size_t)warp * WARP_BYTES;     // [kRing][S, Q][2 KB]
+    T *tile = reinterpret_cast<T *>(ring + RING_BYTES);
     const int64_t ntiles = a.nby * a.nsx;
+    const uint64_t pol = l2_evict_first_policy();
+    int sw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sw[j] = swz_off(lane, j);
+    int slot = 0;
 
     for (;;) {
         uint32_t t = 0;
@@ -565,50 +654,51 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_onepass(OnePass a)
 
         // Vertical: publish the column sums, look back up the slice for V.
         uint64_t vs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, vq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        {
+        uint64_t *inv = a.inc_v + (size_t)t * 512 + lane * 8;
+        if (b > 0) {
             uint64_t *ag = a.agg_v + (size_t)t * 512 + lane * 8;
-            uint64_t *in = a.inc_v + (size_t)t * 512 + lane * 8;
-            if (b > 0) {
-#pragma unroll
-                for (int k = 0; k < 8; k += 2) {
-                    *reinterpret_cast<ulonglong2 *>(ag + k) = make_ulonglong2(cs[k], cs[k + 1]);
-                    if (WQ)
-                        *reinterpret_cast<ulonglong2 *>(ag + 256 + k) =
-                            make_ulonglong2(cq[k], cq[k + 1]);
-                }
-                publish(a.flag_v + t, kAgg);
-                bool ok = true;
-                for (int64_t bb = b - 1; bb >= 0; --bb) {
-                    const int64_t u = bb * a.nsx + s;
-                    const uint32_t f = wait_flag(a.flag_v + u, a.err);
-                    if (!f) { ok = false; break; }
-                    const uint64_t *src = (f == kInc ? a.inc_v : a.agg_v) + (size_t)u * 512 + lane * 8;
-#pragma unroll
-                    for (int k = 0; k < 8; k += 2) {
-                        const ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2 *>(src + k));
-                        vs[k] += w.x; vs[k + 1] += w.y;
-                        if (WQ) {
-                            const ulonglong2 z =
-                                __ldcg(reinterpret_cast<const ulonglong2 *>(src + 256 + k));
-                            vq[k] += z.x; vq[k + 1] += z.y;
-                        }
-                    }
-                    if (f == kInc) break;
-                }
-                if (!ok) break;
-            }
 #pragma unroll
             for (int k = 0; k < 8; k += 2) {
-                *reinterpret_cast<ulonglong2 *>(in + k) =
-                    make_ulonglong2(vs[k] + cs[k], vs[k + 1] + cs[k + 1]);
+                *reinterpret_cast<ulonglong2 *>(ag + k) = make_ulonglong2(cs[k], cs[k + 1]);
                 if (WQ)
-                    *reinterpret_cast<ulonglong2 *>(in + 256 + k) =
-                        make_ulonglong2(vq[k] + cq[k], vq[k + 1] + cq[k + 1]);
+                    *reinterpret_cast<ulonglong2 *>(ag + 256 + k) =
+                        make_ulonglong2(cq[k], cq[k + 1]);
             }
-            publish(a.flag_v + t, kInc);
+            publish(a.flag_v + t, kAgg);
+            bool ok = true;
+            for (int64_t bb = b - 1; bb >= 0; --bb) {
+                const int64_t u = bb * a.nsx + s;
+                const uint32_t f = wait_flag(a.flag_v + u, a.err);
+                if (!f) { ok = false; break; }
+                const uint64_t *src =
+                    (f == kInc ? a.inc_v : a.agg_v) + (size_t)u * 512 + lane * 8;
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) {
+                    const ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2 *>(src + k));
+                    vs[k] += w.x;
+                    vs[k + 1] += w.y;
+                    if (WQ) {
+                        const ulonglong2 z =
+                            __ldcg(reinterpret_cast<const ulonglong2 *>(src + 256 + k));
+                        vq[k] += z.x;
+                        vq[k + 1] += z.y;
+                    }
+                }
+                if (f == kInc) break;
+            }
+            if (!ok) break;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            *reinterpret_cast<ulonglong2 *>(inv + k) =
+                make_ulonglong2(vs[k] + cs[k], vs[k + 1] + cs[k + 1]);
+            if (WQ)
+                *reinterpret_cast<ulonglong2 *>(inv + 256 + k) =
+                    make_ulonglong2(vq[k] + cq[k], vq[k + 1] + cq[k + 1]);
         }
 
-        // Horizontal: own record = (row sums, total of V over the slice).
+        // Horizontal record = (row sums, total of V over the slice); published
+        // with the inclusive vertical record (as inclusive when s == 0).
         uint64_t vt_s = 0, vt_q = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) { vt_s += vs[k]; vt_q += vq[k]; }
@@ -618,33 +708,33 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_onepass(OnePass a)
 #pragma unroll
         for (int j = 0; j < RPL; ++j) { lr_s[j] = 0; lr_q[j] = 0; }
         {
-            uint64_t *ag = a.agg_h + (size_t)t * HREC;
-            uint64_t *in = a.inc_h + (size_t)t * HREC;
-            if (s > 0) {
+            uint64_t *rec = (s > 0 ? a.agg_h : a.inc_h) + (size_t)t * HREC;
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                rec[lane + 32 * j] = rs_s[j];
+                if (WQ) rec[TH + lane + 32 * j] = rs_q[j];
+            }
+            if (lane == 0) { rec[2 * TH] = vt_s; rec[2 * TH + 1] = vt_q; }
+            publish(a.flag_v + t, kInc, a.flag_h + t, s > 0 ? kAgg : kInc);
+        }
+        if (s > 0) {
+            bool ok = true;
+            for (int64_t ss = s - 1; ss >= 0; --ss) {
+                const int64_t u = b * a.nsx + ss;
+                const uint32_t f = wait_flag(a.flag_h + u, a.err);
+                if (!f) { ok = false; break; }
+                const uint64_t *src = (f == kInc ? a.inc_h : a.agg_h) + (size_t)u * HREC;
 #pragma unroll
                 for (int j = 0; j < RPL; ++j) {
-                    ag[lane + 32 * j] = rs_s[j];
-                    if (WQ) ag[TH + lane + 32 * j] = rs_q[j];
+                    lr_s[j] += __ldcg(src + lane + 32 * j);
+                    if (WQ) lr_q[j] += __ldcg(src + TH + lane + 32 * j);
                 }
-                if (lane == 0) { ag[2 * TH] = vt_s; ag[2 * TH + 1] = vt_q; }
-                publish(a.flag_h + t, kAgg);
-                bool ok = true;
-                for (int64_t ss = s - 1; ss >= 0; --ss) {
-                    const int64_t u = b * a.nsx + ss;
-                    const uint32_t f = wait_flag(a.flag_h + u, a.err);
-                    if (!f) { ok = false; break; }
-                    const uint64_t *src = (f == kInc ? a.inc_h : a.agg_h) + (size_t)u * HREC;
-#pragma unroll
-                    for (int j = 0; j < RPL; ++j) {
-                        lr_s[j] += __ldcg(src + lane + 32 * j);
-                        if (WQ) lr_q[j] += __ldcg(src + TH + lane + 32 * j);
-                    }
-                    K_s += __ldcg(src + 2 * TH);
-                    if (WQ) K_q += __ldcg(src + 2 * TH + 1);
-                    if (f == kInc) break;
-                }
-                if (!ok) break;
+                K_s += __ldcg(src + 2 * TH);
+                if (WQ) K_q += __ldcg(src + 2 * TH + 1);
+                if (f == kInc) break;
             }
+            if (!ok) break;
+            uint64_t *in = a.inc_h + (size_t)t * HREC;
 #pragma unroll
             for (int j = 0; j < RPL; ++j) {
                 in[lane + 32 * j] = lr_s[j] + rs_s[j];
@@ -654,7 +744,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_onepass(OnePass a)
             publish(a.flag_h + t, kInc);
         }
 
-        // Scan the staged tile: S = K + H[y] + V*[x] + lp.
+        // Scan the staged tile: S = K + H[y] + V*[x] + lp.  vs/vq become K + V*.
 #pragma unroll
         for (int k = 1; k < 8; ++k) { vs[k] += vs[k - 1]; if (WQ) vq[k] += vq[k - 1]; }
         {
@@ -666,6 +756,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_onepass(OnePass a)
         uint32_t cp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         uint64_t H_s = 0, H_q = 0;
+        const int c1 = (int)(s * (kSliceCols / 16));
         for (int r = 0; r < nr; ++r) {
             uint32_t px[8];
             smem8<T>(tile + r * kSliceCols, lane, px);
@@ -686,24 +777,124 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_onepass(OnePass a)
                     lq8[k] = cqa[k] + (k ? lq8[k - 1] : (QA)0);
                 }
             }
-            const int64_t y = y0 + r;
             const uint32_t is = warp_incl_scan(lp[7], lane);
             const uint64_t base_s = H_s + (uint64_t)(is - lp[7]);
-            uint64_t out[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) out[k] = base_s + vs[k] + lp[k];
-            store8(a.S + y * a.ld, x, a.cols, out);
+            uint64_t base_q = 0;
             if (WQ) {
                 const QA iq = warp_incl_scan(lq8[7], lane);
-                const uint64_t base_q = H_q + (uint64_t)(iq - lq8[7]);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) out[k] = base_q + vq[k] + (uint64_t)lq8[k];
-                store8(a.Q + y * a.ld, x, a.cols, out);
+                base_q = H_q + (uint64_t)(iq - lq8[7]);
             }
+            emit_row<WQ, QA>(ring, slot, sw, base_s, vs, lp, base_q, vq, lq8, &tmS, &tmQ, c1,
+                             (int)(y0 + r), pol);
         }
         __syncwarp();     // the tile buffer is reused by the next ticket
     }
     cp_async_wait_all();
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of a table (rows x ld uint64, ld a multiple of 16) as a 3-D
+// tensor [rows][ld/16][16] with 16 x 16 x 1 boxes in the 128-byte swizzle.
+bool table_tensor_map(CUtensorMap *tm, uint64_t *T, int64_t rows, int64_t ld)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {16, (cuuint64_t)(ld / 16), (cuuint64_t)rows};
+    const cuuint64_t strides[2] = {128, (cuuint64_t)ld * 8};
+    const cuuint32_t box[3] = {16, 16, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, T, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------ launchers --
+constexpr int kTH = 128;   // two-pass rows per tile (u8 tile-local Q sums stay below 2^32)
+
+swa_status launch_error(const char *what, cudaError_t e)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return SWA_ECUDA;
+}
+
+template <typename T, bool WQ, bool VEC>
+swa_status launch_twopass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
+                          char *scratch, cudaStream_t st)
+{
+    Carries c;
+    const int64_t nb = p.nby, ns = p.nsx;
+    c.cs_s = reinterpret_cast<uint64_t *>(scratch + p.off_cs);
+    c.cs_q = c.cs_s + nb * p.ld;
+    c.rs_s = reinterpret_cast<uint64_t *>(scratch + p.off_rs);
+    c.rs_q = c.rs_s + ns * p.rows;
+    c.tt_s = reinterpret_cast<uint64_t *>(scratch + p.off_bt);
+    c.tt_q = c.tt_s + nb * ns;
+    c.tk_s = c.tt_q + nb * ns;
+    c.tk_q = c.tk_s + nb * ns;
+    const int64_t tiles = nb * ns;
+    const int64_t blocks = (tiles + kWarps - 1) / kWarps;
+    CUtensorMap tmS, tmQ;
+    if (!table_tensor_map(&tmS, S, p.rows, p.ld) ||
+        !table_tensor_map(&tmQ, WQ ? Q : S, p.rows, p.ld)) {
+        set_error("cuTensorMapEncodeTiled failed for a %lldx%lld table", (long long)p.rows,
+                  (long long)p.ld);
+        return SWA_ECUDA;
+    }
+    const size_t smem = 1024 + (size_t)kWarps * kRing * 2 * kRowBytes;
+    auto scan = k_scan<T, WQ, VEC, kTH>;
+    cudaError_t e = cudaFuncSetAttribute(scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return launch_error("cudaFuncSetAttribute", e);
+    {
+        LaunchScope ls("sat_reduce", st);
+        k_reduce<T, WQ, VEC, kTH><<<(unsigned)blocks, kWarps * 32, 0, st>>>(
+            img, p.pitch, p.rows, p.cols, p.ld, nb, ns, c);
+    }
+    const int64_t nA = (p.cols + 255) / 256, nB = (p.rows + 255) / 256, nC = (nb + 255) / 256;
+    {
+        LaunchScope ls("sat_carry", st);
+        k_carry<WQ><<<(unsigned)(nA + nB + nC), 256, 0, st>>>(p.rows, p.cols, p.ld, nb, ns,
+                                                              nA, nB, c);
+    }
+    {
+        LaunchScope ls("sat_scan", st);
+        scan<<<(unsigned)blocks, kWarps * 32, smem, st>>>(img, p.pitch, p.rows, p.cols, p.ld,
+                                                           nb, ns, c, tmS, tmQ);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return launch_error("SAT build launch failed", e);
+    return SWA_OK;
+}
+
+template <typename T>
+swa_status dispatch_twopass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
+                            char *scratch, cudaStream_t st)
+{
+    if (p.with_q)
+        return p.vec ? launch_twopass<T, true, true>(p, img, S, Q, scratch, st)
+                     : launch_twopass<T, true, false>(p, img, S, Q, scratch, st);
+    return p.vec ? launch_twopass<T, false, true>(p, img, S, Q, scratch, st)
+                 : launch_twopass<T, false, false>(p, img, S, Q, scratch, st);
 }
 
 template <typename T> constexpr int onepass_rows() { return sizeof(T) == 1 ? 64 : 32; }
@@ -721,8 +912,6 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
     a.ld = p.ld;
     a.nby = p.nby;
     a.nsx = p.nsx;
-    a.S = S;
-    a.Q = Q;
     a.err = err;
     a.ticket = reinterpret_cast<uint32_t *>(scratch + p.off_ticket);
     a.flag_v = reinterpret_cast<uint32_t *>(scratch + p.off_stat);
@@ -732,37 +921,37 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
     a.agg_h = reinterpret_cast<uint64_t *>(scratch + p.off_rs);
     a.inc_h = a.agg_h + (size_t)p.nby * p.nsx * (2 * TH + 2);
     a.stall_tile0 = (test_hooks() & SWA_HOOK_STALL_TILE0) ? 1u : 0u;
-    const size_t smem = (size_t)kWarps * TH * kSliceCols * sizeof(T);
+    CUtensorMap tmS, tmQ;
+    if (!table_tensor_map(&tmS, S, p.rows, p.ld) ||
+        !table_tensor_map(&tmQ, WQ ? Q : S, p.rows, p.ld)) {
+        set_error("cuTensorMapEncodeTiled failed for a %lldx%lld table", (long long)p.rows,
+                  (long long)p.ld);
+        return SWA_ECUDA;
+    }
+    const size_t smem =
+        1024 + (size_t)kOpWarps * (kRing * 2 * kRowBytes + TH * kSliceCols * sizeof(T));
     auto kern = k_onepass<T, WQ, VEC, TH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
-    if (e != cudaSuccess) {
-        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-        return SWA_ECUDA;
-    }
+    if (e != cudaSuccess) return launch_error("cudaFuncSetAttribute", e);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOpWarps * 32, smem);
     if (per_sm < 1) per_sm = 1;
     const int64_t tiles = p.nby * p.nsx;
     int64_t blocks = (int64_t)sms * per_sm;
-    const int64_t need = (tiles + kWarps - 1) / kWarps;
+    const int64_t need = (tiles + kOpWarps - 1) / kOpWarps;
     if (blocks > need) blocks = need;
     if ((e = cudaMemsetAsync(scratch + p.off_ticket, 0, p.off_cs - p.off_ticket, st)) !=
-        cudaSuccess) {
-        set_error("cudaMemsetAsync: %s", cudaGetErrorString(e));
-        return SWA_ECUDA;
-    }
+        cudaSuccess)
+        return launch_error("cudaMemsetAsync", e);
     {
         LaunchScope ls("sat_build", st);
-        kern<<<(unsigned)blocks, kWarps * 32, smem, st>>>(a);
+        kern<<<(unsigned)blocks, kOpWarps * 32, smem, st>>>(a, tmS, tmQ);
     }
     e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        set_error("SAT build launch failed: %s", cudaGetErrorString(e));
-        return SWA_ECUDA;
-    }
+    if (e != cudaSuccess) return launch_error("SAT build launch failed", e);
     return SWA_OK;
 }
 
@@ -792,7 +981,10 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
     p.with_q = (flags & SWA_WITH_SQ) != 0;
     p.twopass = (flags & SWA_TWOPASS) != 0;
     p.ld = (cols + kLdAlign - 1) / kLdAlign * kLdAlign;
-    p.vec = ((uintptr_t)image % 16 == 0) && (pitch % 16 == 0);
+    // 8-pixel vector loads (8 bytes for uint8, 16 for uint16) need the base
+    // address and the pitch aligned to the vector size.
+    const int64_t vbytes = dtype == SWA_U8 ? 8 : 16;
+    p.vec = ((uintptr_t)image % vbytes == 0) && (pitch % vbytes == 0);
     p.th = p.twopass ? kTH : (dtype == SWA_U8 ? onepass_rows<uint8_t>()
                                               : onepass_rows<uint16_t>());
     p.nby = (rows + p.th - 1) / p.th;

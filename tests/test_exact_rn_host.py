@@ -112,3 +112,12 @@ def test_division_correctly_rounded(rn):
         a = int(rng.integers(0, 2**63)) >> int(rng.integers(0, 63))
         want = float(a) / float(n)
         assert rn.rn_div(a, n) == want, (a, n)
+
+
+def test_division_by_powers_of_two_is_exact(rn):
+    rng = np.random.default_rng(13)
+    for k in range(32):
+        n = 1 << k
+        for _ in range(300):
+            a = int(rng.integers(0, 2**63)) >> int(rng.integers(0, 63))
+            assert rn.rn_div(a, n) == float(a) / float(n), (a, n)

@@ -85,13 +85,15 @@ def test_tables_bitexact(dtype, shape, twopass):
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
-@pytest.mark.parametrize("pad,offset", [(5, 1), (13, 0), (0, 3)])
-def test_tables_pitched_and_unaligned(dtype, pad, offset):
-    """Row pitch larger than the width and a base address off 16-byte
-    alignment take the scalar-load path; results must not change."""
+@pytest.mark.parametrize("pad,offset", [(5, 1), (13, 0), (0, 3), (3, 8), (3, 4)])
+@pytest.mark.parametrize("twopass", [False, True])
+def test_tables_pitched_and_unaligned(dtype, pad, offset, twopass):
+    """Row pitches larger than the width and base addresses that are aligned
+    to 8 bytes, 2 bytes or not at all select the vector-load or the
+    pixel-by-pixel path; results must not change."""
     img = rand_img(301, 517, dtype)
     dev = to_device(img, pad_cols=pad, offset_px=offset)
-    sat = swa.build_sat(dev, with_sq=True)
+    sat = swa.build_sat(dev, with_sq=True, twopass=twopass)
     check_tables(sat, img)
     sat.free()
 
