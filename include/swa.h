@@ -107,6 +107,37 @@ swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols,
                          int64_t pitch_bytes, swa_dtype dtype, uint32_t flags,
                          swa_stream stream, swa_sat **out);
 
+/*
+ * The single-pass build of S (and Q) without any device allocation, for
+ * callers that cannot allocate device memory: applications whose own memory
+ * manager reserves the device's memory up front and hands out every buffer,
+ * and code in callbacks or latency-bound loops where an allocation (which may
+ * synchronize the device or fail) is not acceptable.  The paper has no
+ * counterpart; it is an interface variant of swa_build_sat.
+ *   d_image, rows, cols, pitch_bytes, dtype: as swa_build_sat.
+ *   flags        0 or SWA_WITH_SQ (SWA_TWOPASS is not accepted).
+ *   d_S, d_Q     caller-owned device tables of rows x ld uint64 (d_Q only with
+ *                SWA_WITH_SQ), 16-byte aligned; ld >= cols and a multiple of
+ *                16.  Columns cols..ld-1 of each row are scratch that the
+ *                build may overwrite.
+ *   d_status     optional caller-owned device word: set to 0 by the call, and
+ *                bit 0 set by the kernel if a look-back wait expired (the
+ *                tables are then incomplete).  May be NULL.
+ * Scratch lives in one fixed 64 MiB device array inside the library, which
+ * every device that loads the library holds until the process exits.  An
+ * image needing more (about 100 million uint8 or 58 million uint16
+ * pixels) is rejected with SWA_EINVAL and a message; use swa_build_sat.  All
+ * calls share the array: calls whose builds overlap on the GPU (concurrent
+ * streams, or several host threads) race and must be serialized by the
+ * caller.  The first call on each device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Enqueues work on `stream` and returns.
+ */
+swa_status swa_build_sat_noalloc(const void *d_image, int64_t rows, int64_t cols,
+                                 int64_t pitch_bytes, swa_dtype dtype, uint32_t flags,
+                                 uint64_t *d_S, uint64_t *d_Q, int64_t ld,
+                                 uint32_t *d_status, swa_stream stream);
+
 /* Output grid of valid windows (host only, no device work).  SWA_EINVAL when
  * a size or stride is <= 0 or the window is larger than the image. */
 swa_status swa_window_shape(int64_t rows, int64_t cols, int64_t wh, int64_t ww,

@@ -61,6 +61,8 @@ SIGNATURES = {
     "swa_version": (_I32, []),
     "swa_profile_begin": (ctypes.c_int, []),
     "swa_set_test_hooks": (ctypes.c_int, [_U32]),
+    "swa_build_sat_noalloc": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _U32, _VP, _VP,
+                                             _I64, _VP, _VP]),
     "swa_profile_end": (_I32, [_P(swa_kernel_time), _I32]),
 }
 

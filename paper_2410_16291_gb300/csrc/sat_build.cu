@@ -1031,3 +1031,93 @@ swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S, uint
 }
 
 }  // namespace swa
+
+// ------------------------------------------------ allocation-free build --
+// swa_build_sat_noalloc runs the single-pass build with its scratch (tile
+// tickets, flags and look-back records) in this fixed device array instead of
+// memory allocated per call.  The array exists once per device that loads the
+// library and stays allocated until the process exits.  All calls share it,
+// so calls whose builds overlap on the GPU race; each call clears the parts
+// that must start at zero (the ticket and the flags) before its kernel runs.
+namespace swa {
+namespace {
+constexpr int64_t kNoAllocScratchBytes = 64ll << 20;          // 64 MiB
+constexpr int64_t kNoAllocStatusOffset = kNoAllocScratchBytes - 256;
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+char *g_noalloc_ptr[kNoAllocMaxDevices];
+}  // namespace
+}  // namespace swa
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[swa::kNoAllocScratchBytes];
+
+extern "C" swa_status swa_build_sat_noalloc(const void *d_image, int64_t rows, int64_t cols,
+                                           int64_t pitch_bytes, swa_dtype dtype,
+                                           uint32_t flags, uint64_t *d_S, uint64_t *d_Q,
+                                           int64_t ld, uint32_t *d_status, swa_stream stream)
+{
+    using namespace swa;
+    const int64_t pb = dtype == SWA_U16 ? 2 : 1;
+    const bool wq = (flags & SWA_WITH_SQ) != 0;
+    if (!d_image || !d_S || (wq && !d_Q) || rows <= 0 || cols <= 0 ||
+        (dtype != SWA_U8 && dtype != SWA_U16) || (flags & ~(uint32_t)SWA_WITH_SQ) ||
+        pitch_bytes < cols * pb || ld < cols || (ld % 16) || ((uintptr_t)d_S & 15) ||
+        (wq && ((uintptr_t)d_Q & 15)) || ((uintptr_t)d_status & 3)) {
+        set_error("bad arguments to swa_build_sat_noalloc");
+        return SWA_EINVAL;
+    }
+    if (dtype == SWA_U16 && ((uintptr_t)d_image % 2 || pitch_bytes % 2)) {
+        set_error("uint16 images need a 2-byte aligned base and an even pitch");
+        return SWA_EINVAL;
+    }
+    {
+        const unsigned __int128 n = (unsigned __int128)rows * (unsigned __int128)cols;
+        const unsigned __int128 mx = dtype == SWA_U8 ? 255 : 65535;
+        const unsigned __int128 lim = (unsigned __int128)1 << 64;
+        if (n * mx >= lim || (wq && n * mx * mx >= lim)) {
+            set_error("a table entry could exceed 2^64-1");
+            return SWA_EOVERFLOW;
+        }
+    }
+    BuildPlan p = make_plan(rows, cols, pitch_bytes, dtype, flags, d_image);
+    p.ld = ld;
+    if (p.scratch_bytes > kNoAllocStatusOffset) {
+        set_error("swa_build_sat_noalloc: a %lldx%lld image needs %lld bytes of scratch; the "
+                  "fixed array holds %lld (use swa_build_sat)",
+                  (long long)rows, (long long)cols, (long long)p.scratch_bytes,
+                  (long long)kNoAllocStatusOffset);
+        return SWA_EINVAL;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("cudaGetDevice: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    char *scratch = nullptr;
+    {
+        // First call on this device: look up the array's device address
+        // (host code cannot use the symbol itself as a pointer).
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) {
+                set_error("cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+                return SWA_ECUDA;
+            }
+            g_noalloc_ptr[dev] = static_cast<char *>(ptr);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t *status = d_status ? d_status
+                                : reinterpret_cast<uint32_t *>(scratch + kNoAllocStatusOffset);
+    if ((e = cudaMemsetAsync(status, 0, sizeof(uint32_t), st)) != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    const char *img = static_cast<const char *>(d_image);
+    if (dtype == SWA_U8) return dispatch_onepass<uint8_t>(p, img, d_S, d_Q, scratch, status, st);
+    return dispatch_onepass<uint16_t>(p, img, d_S, d_Q, scratch, status, st);
+}
