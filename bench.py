@@ -40,7 +40,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--plain-steps", type=int, default=2,
+                    help="passes of the plain per-request path (workload 3)")
+    ap.add_argument("--no-tune", action="store_true", help="workload 3: default batch config")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -412,6 +415,116 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world, local_rank):
+    """Workload 3: 256 uneven uint8/uint16 images with 1-4 queries each, all
+    built and queried by one persistent launch replayed from a CUDA graph,
+    against the plain per-request path (build, query, free per image, in
+    order on one stream) on the same device-resident images and outputs."""
+    import torch
+
+    import paper_2410_16291_gb300 as swa
+    import synth
+    from paper_2410_16291_gb300 import build as swa_build
+    from paper_2410_16291_gb300 import tune
+    swa_build.build()
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+    imgs = synth.workload(3)
+    t0 = time.perf_counter()
+    devs, wins = [], []
+    for im in imgs:
+        a = im.generate()
+        t = torch.from_numpy(a.view(np.int16) if im.dtype == "u16" else a).cuda()
+        devs.append(t)
+        wins.append([(w.wh, w.ww, w.sy, w.sx) for w in im.windows])
+    gen_s = time.perf_counter() - t0
+    px = sum(im.pixels for im in imgs)
+    n_out = sum(((im.rows - w.wh) // w.sy + 1) * ((im.cols - w.ww) // w.sx + 1)
+                for im in imgs for w in im.windows)
+    cfg = {"u8_tile_rows": 64, "order": 0} if args.no_tune else tune.tune(devs, wins)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = swa.Batch(devs, wins, stream=stream, **cfg)
+        for _ in range(args.warmup):
+            b.run(stream)
+    stream.synchronize()
+    b.sync()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        b.run(stream)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(gpu_id_for_smi(local_rank))
+    if rank == 0:
+        clocks.start()
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    b.sync()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        td.barrier()
+        tt = torch.tensor([ms], device="cuda")
+        td.all_reduce(tt, op=td.ReduceOp.MAX)
+        ms = float(tt.item())
+    clk = clocks.stop() if rank == 0 else None
+
+    # Plain per-request path on the same images and output buffers.
+    def plain_pass():
+        for dev, wl, outs in zip(devs, wins, b.outputs):
+            sat = swa.build_sat(dev, with_sq=True)
+            sat.window_stats(wl, out=outs)
+            sat.free()
+    plain_pass()
+    torch.cuda.synchronize()
+    l0 = swa.lib().swa_launch_count()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for _ in range(args.plain_steps):
+        plain_pass()
+    p1.record()
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1) / args.plain_steps
+    plain_launches = (swa.lib().swa_launch_count() - l0) // args.plain_steps
+    hbm, hbm_kind = peaks()
+    algo = sum(im.pixels * ((2 if im.dtype == "u16" else 1) + 16) for im in imgs) + 24 * n_out
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": world * px / (ms / 1e3) / 1e9, "unit": "Gpx/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "256 uneven synthetic images (sides 512-8192, aspect 0.5-2, "
+                                   "uint8/uint16 50/50), 1-4 windows 16-512 px stride 1-8",
+                       "images": len(imgs), "pixels": px, "window_outputs": n_out,
+                       "batch_config": cfg, "launch": "one persistent kernel per step, "
+                                                      "replayed from a CUDA graph",
+                       "l2": "inputs larger than L2 (%.1f GB of tables)" % (16 * px / 1e9)},
+            "window_outputs_per_s": world * n_out / (ms / 1e3),
+            "plain_path": {"ms_per_pass": plain_ms, "gpx_s": px / (plain_ms / 1e3) / 1e9,
+                           "launches_per_pass": plain_launches},
+            "speedup_vs_plain": plain_ms / ms,
+            "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": algo / (ms / 1e3) / 1e9,
+                         "peak": hbm, "unit": "GB/s", "frac": algo / (ms / 1e3) / 1e9 / hbm,
+                         "peak_kind": hbm_kind, "algorithmic_bytes_per_launch": algo,
+                         "traffic": traffic_record("k_batch")},
+            "plan_bytes": b.nbytes(), "gpu_launches": 2 * args.steps,
+            "host_generation_s": gen_s, "clocks": clk, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+    b.free()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -425,7 +538,10 @@ def main():
         import torch.distributed as td
         torch.cuda.set_device(local_rank)
         td.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    run_ours(args, rank, world, local_rank)
+    if args.workload == 3:
+        run_batch(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as td
         td.destroy_process_group()

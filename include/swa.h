@@ -201,6 +201,57 @@ swa_status swa_analyze(const void *image, int64_t rows, int64_t cols,
                        int64_t pitch_bytes, swa_dtype dtype,
                        const swa_window *windows, int32_t n, swa_stream stream);
 
+/*
+ * Batched engine: many images of uneven sizes and dtypes, each with its own
+ * window queries, built and queried in ONE persistent kernel launch (the
+ * single-pass build of every image, then every query, from one work queue;
+ * a query waits for its image's tables, bounded).  A plan owns the tables of
+ * all images (and the scratch) until swa_batch_free; swa_batch_run only
+ * zeroes its counters and launches the kernel, so it allocates nothing and
+ * can be replayed from a CUDA graph.  Both tables are built for every image.
+ */
+typedef struct {
+    const void *image;          /* device pointer, as for swa_build_sat */
+    int64_t rows, cols, pitch_bytes;
+    swa_dtype dtype;
+    int32_t n_windows;
+    const swa_window *windows;  /* host array; the output pointers are device memory */
+} swa_batch_item;
+
+typedef struct {
+    int32_t u8_tile_rows;       /* rows per uint8 tile: 32 or 64 (0: 64) */
+    int32_t order;              /* 0: images in the given order; 1: largest first */
+    int32_t reserved[6];        /* must be 0 */
+} swa_batch_config;
+
+typedef struct swa_batch swa_batch;
+
+/* Validate the items, allocate tables and scratch for all of them, upload
+ * the work descriptors (waits for that upload on `stream`).  cfg may be
+ * NULL.  SWA_EINVAL / SWA_EOVERFLOW as for swa_build_sat and
+ * swa_window_stats; SWA_ENOMEM if the plan does not fit. */
+swa_status swa_batch_create(const swa_batch_item *items, int32_t n,
+                            const swa_batch_config *cfg, swa_stream stream,
+                            swa_batch **out);
+
+/* Enqueue one pass over the whole batch on `stream`: every table and every
+ * window output is (re)written. */
+swa_status swa_batch_run(swa_batch *b, swa_stream stream);
+
+/* Wait for the plan's stream and report a device-side wait that gave up
+ * (SWA_ETIMEOUT). */
+swa_status swa_batch_sync(swa_batch *b);
+
+/* Device views of item `item`'s tables (as for swa_sat_data). */
+swa_status swa_batch_tables(const swa_batch *b, int32_t item, const uint64_t **d_S,
+                            const uint64_t **d_Q, int64_t *ld);
+
+/* Device bytes the plan holds (-1 for a bad plan). */
+int64_t swa_batch_bytes(const swa_batch *b);
+
+/* Release the plan (stream-ordered on the stream it was created on). */
+void swa_batch_free(swa_batch *b);
+
 /* Process-wide cap on the device bytes this library holds (tables, scratch
  * and staging) on each device; a request beyond it fails with SWA_ENOMEM.
  * A negative value removes the cap (the default). */

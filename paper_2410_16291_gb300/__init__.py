@@ -35,6 +35,17 @@ class swa_window(ctypes.Structure):
                 ("std", _VP), ("out_ld", _I64)]
 
 
+class swa_batch_item(ctypes.Structure):
+    """Mirror of ``swa_batch_item`` in swa.h."""
+    _fields_ = [("image", _VP), ("rows", _I64), ("cols", _I64), ("pitch_bytes", _I64),
+                ("dtype", ctypes.c_int), ("n_windows", _I32), ("windows", _P(swa_window))]
+
+
+class swa_batch_config(ctypes.Structure):
+    """Mirror of ``swa_batch_config`` in swa.h."""
+    _fields_ = [("u8_tile_rows", _I32), ("order", _I32), ("reserved", _I32 * 6)]
+
+
 class swa_kernel_time(ctypes.Structure):
     """Mirror of ``swa_kernel_time`` in swa.h."""
     _fields_ = [("name", ctypes.c_char * 48), ("launches", _I64), ("total_ms", ctypes.c_double),
@@ -61,6 +72,13 @@ SIGNATURES = {
     "swa_version": (_I32, []),
     "swa_profile_begin": (ctypes.c_int, []),
     "swa_set_test_hooks": (ctypes.c_int, [_U32]),
+    "swa_batch_create": (ctypes.c_int, [_P(swa_batch_item), _I32, _P(swa_batch_config), _VP,
+                                        _P(_VP)]),
+    "swa_batch_run": (ctypes.c_int, [_VP, _VP]),
+    "swa_batch_sync": (ctypes.c_int, [_VP]),
+    "swa_batch_tables": (ctypes.c_int, [_VP, _I32, _P(_VP), _P(_VP), _P(_I64)]),
+    "swa_batch_bytes": (_I64, [_VP]),
+    "swa_batch_free": (None, [_VP]),
     "swa_build_sat_noalloc": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _U32, _VP, _VP,
                                              _I64, _VP, _VP]),
     "swa_profile_end": (_I32, [_P(swa_kernel_time), _I32]),
@@ -282,3 +300,87 @@ def analyze(image, windows, outputs=("sum", "mean", "std"), out=None, stream=Non
                             _dtype_code(image), arr, len(windows), _stream_ptr(stream)),
           "swa_analyze")
     return res
+
+
+class Batch:
+    """A batched plan: many images with their window queries, built and
+    queried by one persistent launch per ``run`` (see swa_batch_create).
+
+    images: list of 2-D uint8/uint16 (or int16 bit-pattern) CUDA tensors.
+    windows: list (per image) of [(wh, ww, sy, sx), ...].
+    Outputs are allocated here (device tensors, like SAT.window_stats) unless
+    ``out`` supplies them.
+    """
+
+    def __init__(self, images, windows, outputs=("sum", "mean", "std"), u8_tile_rows=64,
+                 order=0, stream=None, out=None):
+        import torch
+        mask = (SWA_OUT_SUM if "sum" in outputs else 0) | (
+            SWA_OUT_MEAN if "mean" in outputs else 0) | (SWA_OUT_STD if "std" in outputs else 0)
+        self.images = list(images)
+        self.outputs = []
+        self._wins = []
+        items = (swa_batch_item * len(self.images))()
+        for k, (img, wl) in enumerate(zip(self.images, windows)):
+            assert img.is_cuda and img.dim() == 2 and img.stride(1) == 1
+            rows, cols = img.shape
+            arr = (swa_window * max(1, len(wl)))()
+            res = []
+            for q, (wh, ww, sy, sx) in enumerate(wl):
+                R, C = window_shape(rows, cols, wh, ww, sy, sx)
+                if out is not None:
+                    o = out[k][q]
+                else:
+                    o = {}
+                    if mask & SWA_OUT_SUM:
+                        o["sum"] = torch.empty((R, C), dtype=torch.int64, device=img.device)
+                    if mask & SWA_OUT_MEAN:
+                        o["mean"] = torch.empty((R, C), dtype=torch.float64, device=img.device)
+                    if mask & SWA_OUT_STD:
+                        o["std"] = torch.empty((R, C), dtype=torch.float64, device=img.device)
+                ld = next(iter(o.values())).stride(0)
+                arr[q] = swa_window(wh, ww, sy, sx, mask, 0,
+                                    o["sum"].data_ptr() if "sum" in o else None,
+                                    o["mean"].data_ptr() if "mean" in o else None,
+                                    o["std"].data_ptr() if "std" in o else None, ld)
+                res.append(o)
+            self._wins.append(arr)
+            self.outputs.append(res)
+            items[k] = swa_batch_item(img.data_ptr(), rows, cols,
+                                      img.stride(0) * img.element_size(), _dtype_code(img),
+                                      len(wl), arr)
+        cfg = swa_batch_config(u8_tile_rows, order)
+        h = _VP()
+        self.stream = stream
+        check(lib().swa_batch_create(items, len(self.images), ctypes.byref(cfg),
+                                     _stream_ptr(stream), ctypes.byref(h)), "swa_batch_create")
+        self.handle = h.value
+
+    def run(self, stream=None):
+        check(lib().swa_batch_run(self.handle, _stream_ptr(stream if stream is not None
+                                                           else self.stream)), "swa_batch_run")
+
+    def sync(self):
+        check(lib().swa_batch_sync(self.handle), "swa_batch_sync")
+
+    def nbytes(self):
+        return int(lib().swa_batch_bytes(self.handle))
+
+    def tables(self, k):
+        """(S, Q) int64 views (uint64 bit patterns) of image k's tables."""
+        S, Q, ld = _VP(), _VP(), _I64()
+        check(lib().swa_batch_tables(self.handle, k, ctypes.byref(S), ctypes.byref(Q),
+                                     ctypes.byref(ld)), "swa_batch_tables")
+        rows, cols = self.images[k].shape
+        return _view_u64(S.value, rows, cols, ld.value), _view_u64(Q.value, rows, cols, ld.value)
+
+    def free(self):
+        if self.handle:
+            lib().swa_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

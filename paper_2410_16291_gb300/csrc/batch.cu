@@ -1,0 +1,544 @@
+// Batched engine: many images of uneven sizes and dtypes, each with its own
+// window queries, built and queried in ONE persistent kernel launch.
+//
+// Work is a single ticket queue.  Tickets [0, T) are the SAT tiles of all
+// images (image after image, row-major tiles within an image), processed by
+// the single-pass tile routine with decoupled look-back inside each image.
+// Tickets [T, T + W) are window items: one warp evaluates 256 consecutive
+// windows of one output row of one query (8 per lane, 32 apart, so loads and
+// stores stay coalesced).  A window item first waits (bounded) until every
+// tile of its image has been counted as done; a tile is counted only after
+// its bulk table stores have completed.  Window items wait only on tile
+// tickets, which are all smaller, so the queue always makes progress.
+//
+// The launch (zeroing the ticket, flags and counters, then the kernel) does
+// not allocate, so it can be replayed from a CUDA graph.  Every image's
+// tables stay in device memory until swa_batch_free.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "exact_rn.cuh"
+#include "sat_tile.cuh"
+#include "swa_internal.h"
+
+namespace swa {
+namespace {
+
+struct alignas(64) BImg {
+    CUtensorMap tmS, tmQ;             // TMA views of this image's tables
+    const char *img;
+    int64_t pitch, rows, cols, nby, nsx, ld;
+    uint64_t *S, *Q;
+    uint32_t *flag_v, *flag_h;
+    uint64_t *agg_v, *inc_v, *agg_h, *inc_h;
+    uint32_t tile_base, ntiles;
+    int32_t dtype, vec, th;
+};
+
+struct BQuery {
+    WinDesc w;
+    uint64_t n;
+    double n_d;
+    rn::Divisor div;
+    int32_t img, int_rn;
+    int64_t nbx;                      // items per output row
+    uint32_t item_base, nitems;
+};
+
+struct BatchArgs {
+    const BImg *imgs;
+    const BQuery *qs;
+    int32_t nimg, nq;
+    uint32_t total_tiles, total_items;
+    uint32_t *ticket, *err, *done;    // done[nimg]
+};
+
+constexpr int kBatchWarps = 8;
+// Shared memory per warp: the larger of the uint8 (64-row) and uint16 tile
+// routines, so warps working on different dtypes never overlap.
+constexpr int kBatchWarpBytes =
+    onepass_warp_bytes<uint8_t, 64>() > onepass_warp_bytes<uint16_t, 32>()
+        ? onepass_warp_bytes<uint8_t, 64>() : onepass_warp_bytes<uint16_t, 32>();
+constexpr uint32_t kErrBatchWait = 4u;
+
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *tm)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(tm))
+                 : "memory");
+}
+
+// Largest index i in [0, n) with base(i) <= t (bases ascending).
+template <typename F>
+__device__ __forceinline__ int find_base(int n, uint32_t t, F base)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base(mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, bool VEC, int TH>
+__device__ __forceinline__ bool batch_tile(const BImg &im, uint32_t t, uint32_t *err,
+                                           unsigned char *smem_raw)
+{
+    WarpRes<T> w = warp_res<T, TH>(smem_raw, kBatchWarpBytes);
+    TileCtx c;
+    c.img = im.img;
+    c.pitch = im.pitch;
+    c.rows = im.rows;
+    c.cols = im.cols;
+    c.nby = im.nby;
+    c.nsx = im.nsx;
+    c.flag_v = im.flag_v;
+    c.flag_h = im.flag_h;
+    c.agg_v = im.agg_v;
+    c.inc_v = im.inc_v;
+    c.agg_h = im.agg_h;
+    c.inc_h = im.inc_h;
+    c.tmS = &im.tmS;
+    c.tmQ = &im.tmQ;
+    return onepass_tile<T, true, VEC, TH>(c, t, err, w);
+}
+
+// Wait (bounded) until all tiles of image k are done.
+__device__ __noinline__ bool wait_image(const uint32_t *done, uint32_t need, uint32_t *err)
+{
+    uint32_t v = ld_acquire(done);
+    if (__all_sync(kFull, v >= need)) return true;
+    const uint64_t t0 = global_ns();
+    unsigned ns = 128;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 4096) ns <<= 1;
+        v = ld_acquire(done);
+        if (__all_sync(kFull, v >= need)) return true;
+        if (*(volatile uint32_t *)err) return false;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            if ((threadIdx.x & 31) == 0) atomicOr(err, kErrTimeout | kErrBatchWait);
+            __syncwarp();
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void batch_windows(const BQuery &q, const BImg &im, uint32_t item)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = item / q.nbx;
+    const int64_t j0 = (item % q.nbx) * 256;
+    const uint64_t *S = im.S, *Q = im.Q;
+    const int64_t ld = im.ld;
+    const int64_t y0 = i * q.w.sy, y1 = y0 + q.w.wh - 1;
+    const bool top = y0 > 0;
+    const int64_t rt = (y0 - 1) * ld, rb = y1 * ld;
+    const uint32_t o = q.w.outputs;
+#pragma unroll 2
+    for (int m = 0; m < 8; ++m) {
+        const int64_t j = j0 + lane + 32 * m;
+        if (j >= q.w.C) break;
+        const int64_t x0 = j * q.w.sx, x1 = x0 + q.w.ww - 1;
+        const bool left = x0 > 0;
+        uint64_t sw = __ldcg(S + rb + x1);
+        if (top) sw -= __ldcg(S + rt + x1);
+        if (left) sw -= __ldcg(S + rb + x0 - 1);
+        if (top && left) sw += __ldcg(S + rt + x0 - 1);
+        const int64_t oi = i * q.w.out_ld + j;
+        if (o & SWA_OUT_SUM) q.w.sum[oi] = sw;
+        if (o & SWA_OUT_MEAN)
+            q.w.mean[oi] = q.int_rn ? rn::mean_rn(sw, q.div)
+                                    : __ddiv_rn(__ull2double_rn(sw), q.n_d);
+        if (o & SWA_OUT_STD) {
+            uint64_t qw = __ldcg(Q + rb + x1);
+            if (top) qw -= __ldcg(Q + rt + x1);
+            if (left) qw -= __ldcg(Q + rb + x0 - 1);
+            if (top && left) qw += __ldcg(Q + rt + x0 - 1);
+            if (q.int_rn) {
+                q.w.std[oi] = rn::std_rn(q.n, sw, qw, q.div);
+            } else {
+                const unsigned __int128 D =
+                    (unsigned __int128)q.n * qw - (unsigned __int128)sw * sw;
+                const double dd =
+                    rn::fp_to_double(rn::round_u128((uint64_t)(D >> 64), (uint64_t)D));
+                q.w.std[oi] = __ddiv_rn(__dsqrt_rn(dd), q.n_d);
+            }
+        }
+    }
+}
+
+template <int TH8>
+__global__ void __launch_bounds__(kBatchWarps * 32, 1) k_batch(const __grid_constant__ BatchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const uint32_t total = a.total_tiles + a.total_items;
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(a.ticket, 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= total || *(volatile uint32_t *)a.err) break;
+        if (t < a.total_tiles) {
+            const int k = find_base(a.nimg, t, [&](int i) { return a.imgs[i].tile_base; });
+            const BImg &im = a.imgs[k];
+            const uint32_t tl = t - im.tile_base;
+            tensormap_acquire(&im.tmS);
+            tensormap_acquire(&im.tmQ);
+            bool ok;
+            if (im.dtype == SWA_U8)
+                ok = im.vec ? batch_tile<uint8_t, true, TH8>(im, tl, a.err, smem_raw)
+                            : batch_tile<uint8_t, false, TH8>(im, tl, a.err, smem_raw);
+            else
+                ok = im.vec ? batch_tile<uint16_t, true, 32>(im, tl, a.err, smem_raw)
+                            : batch_tile<uint16_t, false, 32>(im, tl, a.err, smem_raw);
+            if (!ok) break;
+            // Count the tile once its table rows are written and visible.
+            if (lane == 0) {
+                bulk_wait_all();
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __threadfence();
+                atomicAdd(a.done + k, 1u);
+            }
+            __syncwarp();
+        } else {
+            const uint32_t ti = t - a.total_tiles;
+            const int qi = find_base(a.nq, ti, [&](int i) { return a.qs[i].item_base; });
+            const BQuery &q = a.qs[qi];
+            const BImg &im = a.imgs[q.img];
+            if (!wait_image(a.done + q.img, im.ntiles, a.err)) break;
+            batch_windows(q, im, ti - q.item_base);
+        }
+    }
+    cp_async_wait_all();
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+}
+
+int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
+
+}  // namespace
+}  // namespace swa
+
+using namespace swa;
+
+struct swa_batch {
+    uint64_t tag;
+    int device;
+    int32_t nimg, nq, th8;
+    uint32_t total_tiles, total_items;
+    char *mem;                        // one allocation: descriptors, state, scratch, tables
+    int64_t mem_bytes;
+    int64_t zero_off, zero_bytes;     // ticket, error word, done counters, flags
+    BatchArgs args;
+    std::vector<int64_t> table_off;   // per image: S offset (Q follows)
+    std::vector<int64_t> ld, rows, cols;
+    cudaStream_t stream;
+};
+
+static const uint64_t kBatchTag = 0x5357414241544348ULL;   // "SWABATCH"
+
+extern "C" {
+
+swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_batch_config *cfg,
+                            swa_stream stream, swa_batch **out)
+{
+    if (out) *out = nullptr;
+    if (!items || n <= 0 || !out) {
+        set_error("bad batch arguments");
+        return SWA_EINVAL;
+    }
+    const int th8 = cfg && cfg->u8_tile_rows ? cfg->u8_tile_rows : 64;
+    if (th8 != 32 && th8 != 64) {
+        set_error("u8_tile_rows must be 32 or 64");
+        return SWA_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // Image order: as given, or largest first.
+    std::vector<int32_t> order(n);
+    for (int32_t i = 0; i < n; ++i) order[i] = i;
+    if (cfg && cfg->order == 1)
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            return items[a].rows * items[a].cols > items[b].rows * items[b].cols;
+        });
+    // Validate and size.
+    int64_t nq = 0, tiles = 0, items_w = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const swa_batch_item &it = items[i];
+        const int64_t pb = it.dtype == SWA_U16 ? 2 : 1;
+        if (!it.image || it.rows <= 0 || it.cols <= 0 ||
+            (it.dtype != SWA_U8 && it.dtype != SWA_U16) || it.pitch_bytes < it.cols * pb ||
+            it.n_windows < 0 || (it.n_windows && !it.windows) ||
+            (it.dtype == SWA_U16 && (((uintptr_t)it.image & 1) || (it.pitch_bytes & 1)))) {
+            set_error("batch item %d: bad image arguments", i);
+            return SWA_EINVAL;
+        }
+        const unsigned __int128 px = (unsigned __int128)it.rows * (unsigned __int128)it.cols;
+        const unsigned __int128 mx = it.dtype == SWA_U8 ? 255 : 65535;
+        if (px * mx * mx >= ((unsigned __int128)1 << 64)) {
+            set_error("batch item %d: a table entry could exceed 2^64-1", i);
+            return SWA_EOVERFLOW;
+        }
+        const int th = it.dtype == SWA_U8 ? th8 : 32;
+        tiles += ((it.rows + th - 1) / th) * ((it.cols + kSliceCols - 1) / kSliceCols);
+        for (int32_t k = 0; k < it.n_windows; ++k) {
+            const swa_window &w = it.windows[k];
+            if (w.wh <= 0 || w.ww <= 0 || w.sy <= 0 || w.sx <= 0 || w.wh > it.rows ||
+                w.ww > it.cols || !w.outputs || (w.outputs & ~7u) ||
+                ((w.outputs & SWA_OUT_SUM) && !w.sum) || ((w.outputs & SWA_OUT_MEAN) && !w.mean) ||
+                ((w.outputs & SWA_OUT_STD) && !w.std)) {
+                set_error("batch item %d window %d: bad query", i, k);
+                return SWA_EINVAL;
+            }
+            const int64_t R = (it.rows - w.wh) / w.sy + 1, C = (it.cols - w.ww) / w.sx + 1;
+            if (w.out_ld < C) {
+                set_error("batch item %d window %d: out_ld < %lld", i, k, (long long)C);
+                return SWA_EINVAL;
+            }
+            items_w += R * ((C + 255) / 256);
+            ++nq;
+        }
+    }
+    if (tiles + items_w >= 0xffffffffLL) {
+        set_error("batch too large: %lld work items", (long long)(tiles + items_w));
+        return SWA_EINVAL;
+    }
+    // Layout of the single allocation.
+    int64_t off = 0;
+    const int64_t off_imgs = off;
+    off = align256(off + (int64_t)sizeof(BImg) * n);
+    const int64_t off_qs = off;
+    off = align256(off + (int64_t)sizeof(BQuery) * (nq ? nq : 1));
+    const int64_t zero_off = off;                      // ticket, err, done[n], flags
+    const int64_t off_ticket = off, off_err = off + 4;
+    const int64_t off_done = off + 256;
+    off = off_done + 4 * (int64_t)n;
+    const int64_t off_flags = align256(off);
+    off = off_flags + 2 * 4 * tiles;
+    const int64_t zero_bytes = off - zero_off;
+    off = align256(off);
+    std::vector<BImg> himg(n);
+    std::vector<BQuery> hq(nq ? nq : 1);
+    swa_batch *b = new (std::nothrow) swa_batch();
+    if (!b) return SWA_ENOMEM;
+    b->tag = kBatchTag;
+    b->nimg = n;
+    b->nq = (int32_t)nq;
+    b->th8 = th8;
+    b->table_off.resize(n);
+    b->ld.resize(n);
+    b->rows.resize(n);
+    b->cols.resize(n);
+    b->stream = s;
+    // Records and tables: offsets first, pointers after the allocation.
+    std::vector<int64_t> off_flag(n), off_rec_v(n), off_rec_h(n), off_tab(n);
+    uint32_t tile_base = 0, flag_i = 0;
+    for (int32_t pos = 0; pos < n; ++pos) {
+        const int32_t i = order[pos];
+        const swa_batch_item &it = items[i];
+        const int th = it.dtype == SWA_U8 ? th8 : 32;
+        BImg &m = himg[pos];
+        memset(&m, 0, sizeof(m));
+        m.rows = it.rows;
+        m.cols = it.cols;
+        m.pitch = it.pitch_bytes;
+        m.img = static_cast<const char *>(it.image);
+        m.dtype = it.dtype;
+        m.th = th;
+        const int64_t vb = it.dtype == SWA_U8 ? 8 : 16;
+        m.vec = ((uintptr_t)it.image % vb == 0) && (it.pitch_bytes % vb == 0);
+        m.nby = (it.rows + th - 1) / th;
+        m.nsx = (it.cols + kSliceCols - 1) / kSliceCols;
+        m.ld = (it.cols + kLdAlign - 1) / kLdAlign * kLdAlign;
+        m.ntiles = (uint32_t)(m.nby * m.nsx);
+        m.tile_base = tile_base;
+        tile_base += m.ntiles;
+        off_flag[pos] = off_flags + 4 * (int64_t)flag_i;
+        flag_i += 2 * m.ntiles;
+        off_rec_v[pos] = off;
+        off = align256(off + 2 * (int64_t)m.ntiles * 512 * 8);
+        off_rec_h[pos] = off;
+        off = align256(off + 2 * (int64_t)m.ntiles * (2 * th + 2) * 8);
+    }
+    for (int32_t pos = 0; pos < n; ++pos) {
+        off_tab[pos] = off;
+        off = align256(off + 2 * himg[pos].rows * himg[pos].ld * 8);
+    }
+    b->mem_bytes = off;
+    swa_status st = SWA_OK;
+    void *mem = nullptr;
+    if (dev_alloc(&mem, off, s, &st) != cudaSuccess) {
+        delete b;
+        return st;
+    }
+    b->mem = static_cast<char *>(mem);
+    cudaGetDevice(&b->device);
+    char *base = b->mem;
+    for (int32_t pos = 0; pos < n; ++pos) {
+        BImg &m = himg[pos];
+        const int th = m.th;
+        m.flag_v = reinterpret_cast<uint32_t *>(base + off_flag[pos]);
+        m.flag_h = m.flag_v + m.ntiles;
+        m.agg_v = reinterpret_cast<uint64_t *>(base + off_rec_v[pos]);
+        m.inc_v = m.agg_v + (size_t)m.ntiles * 512;
+        m.agg_h = reinterpret_cast<uint64_t *>(base + off_rec_h[pos]);
+        m.inc_h = m.agg_h + (size_t)m.ntiles * (2 * th + 2);
+        m.S = reinterpret_cast<uint64_t *>(base + off_tab[pos]);
+        m.Q = m.S + m.rows * m.ld;
+        if (!table_tensor_map(&m.tmS, m.S, m.rows, m.ld) ||
+            !table_tensor_map(&m.tmQ, m.Q, m.rows, m.ld)) {
+            set_error("cuTensorMapEncodeTiled failed for batch image %d", order[pos]);
+            dev_free(b->mem, b->mem_bytes, s);
+            delete b;
+            return SWA_ECUDA;
+        }
+        b->table_off[order[pos]] = off_tab[pos];
+        b->ld[order[pos]] = m.ld;
+        b->rows[order[pos]] = m.rows;
+        b->cols[order[pos]] = m.cols;
+    }
+    // Queries in image order.
+    uint32_t item_base = 0;
+    int64_t qk = 0;
+    for (int32_t pos = 0; pos < n; ++pos) {
+        const swa_batch_item &it = items[order[pos]];
+        for (int32_t k = 0; k < it.n_windows; ++k) {
+            const swa_window &w = it.windows[k];
+            BQuery &q = hq[qk++];
+            memset(&q, 0, sizeof(q));
+            q.w.wh = w.wh;
+            q.w.ww = w.ww;
+            q.w.sy = w.sy;
+            q.w.sx = w.sx;
+            q.w.R = (it.rows - w.wh) / w.sy + 1;
+            q.w.C = (it.cols - w.ww) / w.sx + 1;
+            q.w.out_ld = w.out_ld;
+            q.w.outputs = w.outputs;
+            q.w.sum = w.sum;
+            q.w.mean = w.mean;
+            q.w.std = w.std;
+            q.n = (uint64_t)(w.wh * w.ww);
+            q.n_d = (double)q.n;
+            q.int_rn = q.n < (1ull << 32);
+            q.div = rn::make_divisor(q.int_rn ? (uint32_t)q.n : 1u);
+            q.img = pos;
+            q.nbx = (q.w.C + 255) / 256;
+            q.item_base = item_base;
+            q.nitems = (uint32_t)(q.w.R * q.nbx);
+            item_base += q.nitems;
+        }
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(base + off_imgs, himg.data(), sizeof(BImg) * n,
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (nq && (e = cudaMemcpyAsync(base + off_qs, hq.data(), sizeof(BQuery) * nq,
+                                    cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        set_error("uploading batch descriptors: %s", cudaGetErrorString(e));
+        dev_free(b->mem, b->mem_bytes, s);
+        delete b;
+        return SWA_ECUDA;
+    }
+    b->zero_off = zero_off;
+    b->zero_bytes = zero_bytes;
+    b->total_tiles = tile_base;
+    b->total_items = item_base;
+    BatchArgs &a = b->args;
+    a.imgs = reinterpret_cast<const BImg *>(base + off_imgs);
+    a.qs = reinterpret_cast<const BQuery *>(base + off_qs);
+    a.nimg = n;
+    a.nq = (int32_t)nq;
+    a.total_tiles = tile_base;
+    a.total_items = item_base;
+    a.ticket = reinterpret_cast<uint32_t *>(base + off_ticket);
+    a.err = reinterpret_cast<uint32_t *>(base + off_err);
+    a.done = reinterpret_cast<uint32_t *>(base + off_done);
+    *out = b;
+    return SWA_OK;
+}
+
+swa_status swa_batch_run(swa_batch *b, swa_stream stream)
+{
+    if (!b || b->tag != kBatchTag) return SWA_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b->mem + b->zero_off, 0, (size_t)b->zero_bytes, s);
+    if (e != cudaSuccess) {
+        set_error("cudaMemsetAsync: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    const size_t smem = 1024 + (size_t)kBatchWarps * kBatchWarpBytes;
+    auto kern = b->th8 == 64 ? k_batch<64> : k_batch<32>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess) {
+        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    const int64_t work = (int64_t)b->total_tiles + b->total_items;
+    int64_t blocks = std::min<int64_t>(sms, (work + kBatchWarps - 1) / kBatchWarps);
+    if (blocks < 1) blocks = 1;
+    {
+        LaunchScope ls("batch", s);
+        kern<<<(unsigned)blocks, kBatchWarps * 32, smem, s>>>(b->args);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("batch launch failed: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    return SWA_OK;
+}
+
+swa_status swa_batch_sync(swa_batch *b)
+{
+    if (!b || b->tag != kBatchTag) return SWA_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        set_error("synchronize: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    uint32_t err = 0;
+    if ((e = cudaMemcpy(&err, b->args.err, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+        set_error("reading the batch error word: %s", cudaGetErrorString(e));
+        return SWA_ECUDA;
+    }
+    if (err) {
+        set_error("a batch wait exceeded its limit (0x%x)", err);
+        return SWA_ETIMEOUT;
+    }
+    return SWA_OK;
+}
+
+swa_status swa_batch_tables(const swa_batch *b, int32_t item, const uint64_t **d_S,
+                            const uint64_t **d_Q, int64_t *ld)
+{
+    if (!b || b->tag != kBatchTag || item < 0 || item >= b->nimg) return SWA_EINVAL;
+    const uint64_t *S = reinterpret_cast<const uint64_t *>(b->mem + b->table_off[item]);
+    if (d_S) *d_S = S;
+    if (d_Q) *d_Q = S + b->rows[item] * b->ld[item];
+    if (ld) *ld = b->ld[item];
+    return SWA_OK;
+}
+
+int64_t swa_batch_bytes(const swa_batch *b)
+{
+    return (b && b->tag == kBatchTag) ? b->mem_bytes : -1;
+}
+
+void swa_batch_free(swa_batch *b)
+{
+    if (!b || b->tag != kBatchTag) return;
+    dev_free(b->mem, b->mem_bytes, b->stream);
+    b->tag = 0;
+    delete b;
+}
+
+}  // extern "C"

@@ -302,6 +302,16 @@ SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
     return Fp{R, e};
 }
 
+// The double sig * 2^exp exactly (sig < 2^53; the exponent stays normal).
+SWA_HD double fp_to_double(Fp f)
+{
+    if (!f.sig) return 0.0;
+    const int L = 64 - clz64(f.sig);
+    const uint64_t M = f.sig << (53 - L);
+    const int E = L - 1 + f.exp;
+    return bits_to_double(((uint64_t)(E + 1023) << 52) | (M & ((1ull << 52) - 1)));
+}
+
 // mean and std of one window from its exact moments (n < 2^32, n >= 1).
 SWA_HD double mean_rn(uint64_t sw, const Divisor &D)
 {
