@@ -40,7 +40,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--requests", type=int, default=200, help="workload 4: requests")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="workload 4: HBM budget")
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="passes of the plain per-request path (workload 3)")
     ap.add_argument("--no-tune", action="store_true", help="workload 3: default batch config")
@@ -130,6 +132,24 @@ def gpu_id_for_smi(local_rank):
         if local_rank < len(ids):
             return ids[local_rank]
     return local_rank
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The maximum of `value` over all ranks (the slowest rank's time): the
+    job's time under weak scaling.  Without a process group it is `value`."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return world * units_per_rank / seconds
 
 
 def distinct_corner_bytes(rows, cols, wh, ww, sy, sx, tables):
@@ -333,11 +353,7 @@ def run_ours(args, rank, world, local_rank):
     launches = swa.lib().swa_launch_count() - l0
     if dist:
         td.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device="cuda")
     clk = clocks.stop() if rank == 0 else None
 
     # Per-kernel averages and the dominant kernel's roofline.
@@ -384,12 +400,8 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.e2e_steps):
             swa.analyze(host, windows, out=hout)
         torch.cuda.synchronize()
-        et = (time.perf_counter() - t0) / args.e2e_steps
-        if dist:
-            t = torch.tensor([et], device="cuda")
-            td.all_reduce(t, op=td.ReduceOp.MAX)
-            et = float(t.item())
-        e2e = {"value": world * px / et / 1e9, "unit": "Gpx/s",
+        et = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, device="cuda")
+        e2e = {"value": job_throughput(px, et, world) / 1e9, "unit": "Gpx/s",
                "h2d_bytes_per_step": px, "d2h_bytes_per_step": 24 * n_out,
                "ms_per_step": et * 1e3, "steps": args.e2e_steps,
                "api": "swa_analyze (pinned host image in, pinned host results out)"}
@@ -400,7 +412,7 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    value = world * px / (ms / 1e3) / 1e9
+    value = job_throughput(px, ms / 1e3, world) / 1e9
     line = {"metric": METRIC, "value": value, "unit": "Gpx/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -472,12 +484,9 @@ def run_batch(args, rank, world, local_rank):
         e1.record(stream)
     torch.cuda.synchronize()
     b.sync()
-    ms = e0.elapsed_time(e1) / args.steps
     if dist:
         td.barrier()
-        tt = torch.tensor([ms], device="cuda")
-        td.all_reduce(tt, op=td.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device="cuda")
     clk = clocks.stop() if rank == 0 else None
 
     # Plain per-request path on the same images and output buffers.
@@ -508,8 +517,8 @@ def run_batch(args, rank, world, local_rank):
             "config": {"workload": "256 uneven synthetic images (sides 512-8192, aspect 0.5-2, "
                                    "uint8/uint16 50/50), 1-4 windows 16-512 px stride 1-8",
                        "images": len(imgs), "pixels": px, "window_outputs": n_out,
-                       "batch_config": cfg, "launch": "one persistent kernel per step, "
-                                                      "replayed from a CUDA graph",
+                       "batch_config": cfg, "launch": "one persistent build launch + one query launch per step, "
+                                                      "replayed as one CUDA graph",
                        "l2": "inputs larger than L2 (%.1f GB of tables)" % (16 * px / 1e9)},
             "window_outputs_per_s": world * n_out / (ms / 1e3),
             "plain_path": {"ms_per_pass": plain_ms, "gpx_s": px / (plain_ms / 1e3) / 1e9,
@@ -523,6 +532,75 @@ def run_batch(args, rank, world, local_rank):
             "host_generation_s": gen_s, "clocks": clk, "cpu_baseline": None, "e2e": None}
     print(json.dumps(line), flush=True)
     b.free()
+
+
+def run_serve(args, rank, world, local_rank):
+    """Workload 4: a Poisson request stream (200 req/s) over a pool of 64
+    images (sides 1,000-40,000, uint8/uint16), each request 1-8 windows with
+    sum/mean/std, served by the continuous-batching server under a 120 GB
+    budget with resident tables, against the plain per-request path on the
+    same trace."""
+    import torch
+
+    import synth
+    from paper_2410_16291_gb300 import build as swa_build
+    from paper_2410_16291_gb300 import serve
+    swa_build.build()
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    pool, trace = synth.serve_requests(args.requests, synth.DEFAULT_SEED + 4)
+    t0 = time.perf_counter()
+    host = {}
+    for _, idx, _ in trace:
+        if idx in host:
+            continue
+        im = pool[idx]
+        a = im.generate()
+        t = torch.from_numpy(a.view(np.int16) if im.dtype == "u16" else a).pin_memory()
+        host[idx] = t
+    gen_s = time.perf_counter() - t0
+
+    def requests():
+        return [serve.Request(k, idx, host[idx], [(w.wh, w.ww, w.sy, w.sx) for w in wl],
+                              arrival=t) for k, (t, idx, wl) in enumerate(trace)]
+    px = sum(pool[idx].pixels for _, idx, _ in trace)
+    n_out = sum(((pool[idx].rows - w.wh) // w.sy + 1) * ((pool[idx].cols - w.ww) // w.sx + 1)
+                for _, idx, wl in trace for w in wl)
+    # warm-up: one small request through each path
+    small = min(host, key=lambda k: pool[k].pixels)
+    warm = [serve.Request(-1, small, host[small], [(16, 16, 4, 4)])]
+    sv = serve.Server(int(args.budget_gb * 1e9), streams=4, slots=8, keep_results=False)
+    sv.run(warm, realtime=False)
+    serve.plain_path([serve.Request(-2, small, host[small], [(16, 16, 4, 4)])], realtime=False)
+    sv.cache.clear()
+    reqs = requests()
+    t_srv = sv.run(reqs, realtime=True)
+    srv = serve.latency_summary(reqs)
+    hits, misses, evictions = sv.hits, sv.misses, sv.evictions
+    sv.close()
+    torch.cuda.synchronize()
+    preqs = requests()
+    t_plain = serve.plain_path(preqs, realtime=True, keep_results=False)
+    plain = serve.latency_summary(preqs)
+    n = len(reqs)
+    line = {"metric": METRIC, "value": px / t_srv / 1e9, "unit": "Gpx/s", "n_gpus": 1,
+            "steps": n, "warmup": 1, "ms_per_step": t_srv / n * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "served: Poisson 200 req/s over 64 images (sides "
+                                   "1,000-40,000, uint8/uint16), 1-8 windows 16-1024 px, "
+                                   "stride 4-16, sum/mean/std",
+                       "requests": n, "budget_gb": args.budget_gb, "streams": 4, "slots": 8,
+                       "image_pixels_requested": px, "window_outputs": n_out},
+            "served": dict(srv, seconds=t_srv, requests_per_s=n / t_srv,
+                           window_outputs_per_s=n_out / t_srv, cache_hits=hits,
+                           cache_misses=misses, evictions=evictions),
+            "plain_path": dict(plain, seconds=t_plain, requests_per_s=n / t_plain,
+                               window_outputs_per_s=n_out / t_plain),
+            "throughput_vs_plain": t_plain / t_srv, "host_generation_s": gen_s,
+            "window_outputs_per_s": n_out / t_srv, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -540,6 +618,8 @@ def main():
         td.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     if args.workload == 3:
         run_batch(args, rank, world, local_rank)
+    elif args.workload == 4:
+        run_serve(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -203,12 +203,13 @@ swa_status swa_analyze(const void *image, int64_t rows, int64_t cols,
 
 /*
  * Batched engine: many images of uneven sizes and dtypes, each with its own
- * window queries, built and queried in ONE persistent kernel launch (the
- * single-pass build of every image, then every query, from one work queue;
- * a query waits for its image's tables, bounded).  A plan owns the tables of
- * all images (and the scratch) until swa_batch_free; swa_batch_run only
- * zeroes its counters and launches the kernel, so it allocates nothing and
- * can be replayed from a CUDA graph.  Both tables are built for every image.
+ * window queries.  A run is one persistent launch that builds the tables of
+ * every image (the single-pass build, all images' tiles in one work queue),
+ * followed by one launch that evaluates every query of every image.  A plan
+ * owns the tables of all images (and the scratch) until swa_batch_free;
+ * swa_batch_run only zeroes its counters and enqueues the two kernels, so it
+ * allocates nothing and can be replayed from a CUDA graph.  Both tables are
+ * built for every image.
  */
 typedef struct {
     const void *image;          /* device pointer, as for swa_build_sat */

@@ -1,19 +1,20 @@
 // Batched engine: many images of uneven sizes and dtypes, each with its own
-// window queries, built and queried in ONE persistent kernel launch.
+// window queries, in two launches that replay as one CUDA graph:
 //
-// Work is a single ticket queue.  Tickets [0, T) are the SAT tiles of all
-// images (image after image, row-major tiles within an image), processed by
-// the single-pass tile routine with decoupled look-back inside each image.
-// Tickets [T, T + W) are window items: one warp evaluates 256 consecutive
-// windows of one output row of one query (8 per lane, 32 apart, so loads and
-// stores stay coalesced).  A window item first waits (bounded) until every
-// tile of its image has been counted as done; a tile is counted only after
-// its bulk table stores have completed.  Window items wait only on tile
-// tickets, which are all smaller, so the queue always makes progress.
+//  1. k_batch: ONE persistent launch builds every image's tables.  Its work
+//     is a single ticket queue over the SAT tiles of all images (image after
+//     image, row-major tiles within an image), each processed by the
+//     single-pass tile routine with decoupled look-back inside its image.
+//  2. k_batch_windows: one launch evaluates every query of every image; a
+//     block covers 1024 consecutive windows of one output row of one query
+//     and finds its query by binary search over the queries' block offsets.
 //
-// The launch (zeroing the ticket, flags and counters, then the kernel) does
-// not allocate, so it can be replayed from a CUDA graph.  Every image's
-// tables stay in device memory until swa_batch_free.
+// The windows run in a launch of their own because the build's tiles need
+// 24 KB of shared memory per warp (8 warps per SM), while the window
+// arithmetic is ALU-bound and wants full occupancy.  A run (zeroing the
+// ticket and flags, then the two kernels) allocates nothing, so it can be
+// replayed from a CUDA graph.  Every image's tables stay in device memory
+// until swa_batch_free.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -47,8 +48,8 @@ struct BQuery {
     double n_d;
     rn::Divisor div;
     int32_t img, int_rn;
-    int64_t nbx;                      // items per output row
-    uint32_t item_base, nitems;
+    int64_t nbx;                      // blocks per output row
+    uint32_t item_base, nitems;       // first block, blocks
 };
 
 struct BatchArgs {
@@ -56,7 +57,7 @@ struct BatchArgs {
     const BQuery *qs;
     int32_t nimg, nq;
     uint32_t total_tiles, total_items;
-    uint32_t *ticket, *err, *done;    // done[nimg]
+    uint32_t *ticket, *err;
 };
 
 constexpr int kBatchWarps = 8;
@@ -65,7 +66,6 @@ constexpr int kBatchWarps = 8;
 constexpr int kBatchWarpBytes =
     onepass_warp_bytes<uint8_t, 64>() > onepass_warp_bytes<uint16_t, 32>()
         ? onepass_warp_bytes<uint8_t, 64>() : onepass_warp_bytes<uint16_t, 32>();
-constexpr uint32_t kErrBatchWait = 4u;
 
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *tm)
 {
@@ -110,58 +110,49 @@ __device__ __forceinline__ bool batch_tile(const BImg &im, uint32_t t, uint32_t 
     return onepass_tile<T, true, VEC, TH>(c, t, err, w);
 }
 
-// Wait (bounded) until all tiles of image k are done.
-__device__ __noinline__ bool wait_image(const uint32_t *done, uint32_t need, uint32_t *err)
-{
-    uint32_t v = ld_acquire(done);
-    if (__all_sync(kFull, v >= need)) return true;
-    const uint64_t t0 = global_ns();
-    unsigned ns = 128;
-    for (;;) {
-        __nanosleep(ns);
-        if (ns < 4096) ns <<= 1;
-        v = ld_acquire(done);
-        if (__all_sync(kFull, v >= need)) return true;
-        if (*(volatile uint32_t *)err) return false;
-        if (global_ns() - t0 > kWaitLimitNs) {
-            if ((threadIdx.x & 31) == 0) atomicOr(err, kErrTimeout | kErrBatchWait);
-            __syncwarp();
-            return false;
-        }
-    }
-}
+constexpr int kBWinPerThread = 4;
+constexpr int kBWinPerBlock = 256 * kBWinPerThread;
 
-__device__ __forceinline__ void batch_windows(const BQuery &q, const BImg &im, uint32_t item)
+// Queries of all images: block -> query by binary search, then 1024
+// consecutive windows of one output row (thread t: t, t+256, t+512, t+768).
+__global__ void __launch_bounds__(256) k_batch_windows(const BQuery *__restrict__ qs, int32_t nq,
+                                                       const BImg *__restrict__ imgs)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = item / q.nbx;
-    const int64_t j0 = (item % q.nbx) * 256;
-    const uint64_t *S = im.S, *Q = im.Q;
+    const uint32_t bid = blockIdx.x;
+    const int qi = find_base(nq, bid, [&](int i) { return qs[i].item_base; });
+    const BQuery &q = qs[qi];
+    const BImg &im = imgs[q.img];
+    const uint32_t blk = bid - q.item_base;
+    const uint32_t nbx = (uint32_t)q.nbx;
+    const uint32_t i = blk / nbx;
+    const int64_t jb = (int64_t)(blk - i * nbx) * kBWinPerBlock + threadIdx.x;
     const int64_t ld = im.ld;
-    const int64_t y0 = i * q.w.sy, y1 = y0 + q.w.wh - 1;
+    const int64_t y0 = (int64_t)i * q.w.sy, y1 = y0 + q.w.wh - 1;
     const bool top = y0 > 0;
-    const int64_t rt = (y0 - 1) * ld, rb = y1 * ld;
+    const uint64_t *St = im.S + (y0 - 1) * ld, *Sb = im.S + y1 * ld;
+    const uint64_t *Qt = im.Q + (y0 - 1) * ld, *Qb = im.Q + y1 * ld;
     const uint32_t o = q.w.outputs;
-#pragma unroll 2
-    for (int m = 0; m < 8; ++m) {
-        const int64_t j = j0 + lane + 32 * m;
+    const int64_t orow = (int64_t)i * q.w.out_ld;
+#pragma unroll
+    for (int m = 0; m < kBWinPerThread; ++m) {
+        const int64_t j = jb + 256 * m;
         if (j >= q.w.C) break;
         const int64_t x0 = j * q.w.sx, x1 = x0 + q.w.ww - 1;
         const bool left = x0 > 0;
-        uint64_t sw = __ldcg(S + rb + x1);
-        if (top) sw -= __ldcg(S + rt + x1);
-        if (left) sw -= __ldcg(S + rb + x0 - 1);
-        if (top && left) sw += __ldcg(S + rt + x0 - 1);
-        const int64_t oi = i * q.w.out_ld + j;
+        uint64_t sw = __ldg(Sb + x1);
+        if (top) sw -= __ldg(St + x1);
+        if (left) sw -= __ldg(Sb + x0 - 1);
+        if (top && left) sw += __ldg(St + x0 - 1);
+        const int64_t oi = orow + j;
         if (o & SWA_OUT_SUM) q.w.sum[oi] = sw;
         if (o & SWA_OUT_MEAN)
             q.w.mean[oi] = q.int_rn ? rn::mean_rn(sw, q.div)
                                     : __ddiv_rn(__ull2double_rn(sw), q.n_d);
         if (o & SWA_OUT_STD) {
-            uint64_t qw = __ldcg(Q + rb + x1);
-            if (top) qw -= __ldcg(Q + rt + x1);
-            if (left) qw -= __ldcg(Q + rb + x0 - 1);
-            if (top && left) qw += __ldcg(Q + rt + x0 - 1);
+            uint64_t qw = __ldg(Qb + x1);
+            if (top) qw -= __ldg(Qt + x1);
+            if (left) qw -= __ldg(Qb + x0 - 1);
+            if (top && left) qw += __ldg(Qt + x0 - 1);
             if (q.int_rn) {
                 q.w.std[oi] = rn::std_rn(q.n, sw, qw, q.div);
             } else {
@@ -175,47 +166,33 @@ __device__ __forceinline__ void batch_windows(const BQuery &q, const BImg &im, u
     }
 }
 
+// Builds: one persistent launch over the tiles of every image.
 template <int TH8>
 __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_batch(const __grid_constant__ BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
-    const uint32_t total = a.total_tiles + a.total_items;
     for (;;) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(a.ticket, 1u);
         t = __shfl_sync(kFull, t, 0);
-        if (t >= total || *(volatile uint32_t *)a.err) break;
-        if (t < a.total_tiles) {
-            const int k = find_base(a.nimg, t, [&](int i) { return a.imgs[i].tile_base; });
-            const BImg &im = a.imgs[k];
-            const uint32_t tl = t - im.tile_base;
-            tensormap_acquire(&im.tmS);
-            tensormap_acquire(&im.tmQ);
-            bool ok;
-            if (im.dtype == SWA_U8)
-                ok = im.vec ? batch_tile<uint8_t, true, TH8>(im, tl, a.err, smem_raw)
-                            : batch_tile<uint8_t, false, TH8>(im, tl, a.err, smem_raw);
-            else
-                ok = im.vec ? batch_tile<uint16_t, true, 32>(im, tl, a.err, smem_raw)
-                            : batch_tile<uint16_t, false, 32>(im, tl, a.err, smem_raw);
-            if (!ok) break;
-            // Count the tile once its table rows are written and visible.
-            if (lane == 0) {
-                bulk_wait_all();
-                asm volatile("fence.proxy.async.global;" ::: "memory");
-                __threadfence();
-                atomicAdd(a.done + k, 1u);
-            }
-            __syncwarp();
-        } else {
-            const uint32_t ti = t - a.total_tiles;
-            const int qi = find_base(a.nq, ti, [&](int i) { return a.qs[i].item_base; });
-            const BQuery &q = a.qs[qi];
-            const BImg &im = a.imgs[q.img];
-            if (!wait_image(a.done + q.img, im.ntiles, a.err)) break;
-            batch_windows(q, im, ti - q.item_base);
-        }
+        if (t >= a.total_tiles || *(volatile uint32_t *)a.err) break;
+        const int k = find_base(a.nimg, t, [&](int i) { return a.imgs[i].tile_base; });
+        const BImg &im = a.imgs[k];
+        const uint32_t tl = t - im.tile_base;
+        tensormap_acquire(&im.tmS);
+        tensormap_acquire(&im.tmQ);
+        bool ok;
+        if (im.dtype == SWA_U8)
+            ok = im.vec ? batch_tile<uint8_t, true, TH8>(im, tl, a.err, smem_raw)
+                        : batch_tile<uint8_t, false, TH8>(im, tl, a.err, smem_raw);
+        else
+            ok = im.vec ? batch_tile<uint16_t, true, 32>(im, tl, a.err, smem_raw)
+                        : batch_tile<uint16_t, false, 32>(im, tl, a.err, smem_raw);
+        if (!ok) break;
+        // the next ticket reuses the ring from slot 0
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
     }
     cp_async_wait_all();
     if (lane == 0) bulk_wait_all();
@@ -236,7 +213,7 @@ struct swa_batch {
     uint32_t total_tiles, total_items;
     char *mem;                        // one allocation: descriptors, state, scratch, tables
     int64_t mem_bytes;
-    int64_t zero_off, zero_bytes;     // ticket, error word, done counters, flags
+    int64_t zero_off, zero_bytes;     // ticket, error word, flags
     BatchArgs args;
     std::vector<int64_t> table_off;   // per image: S offset (Q follows)
     std::vector<int64_t> ld, rows, cols;
@@ -302,11 +279,11 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
                 set_error("batch item %d window %d: out_ld < %lld", i, k, (long long)C);
                 return SWA_EINVAL;
             }
-            items_w += R * ((C + 255) / 256);
+            items_w += R * ((C + kBWinPerBlock - 1) / kBWinPerBlock);
             ++nq;
         }
     }
-    if (tiles + items_w >= 0xffffffffLL) {
+    if (tiles >= 0xffffffffLL || items_w >= 0x7fffffffLL) {
         set_error("batch too large: %lld work items", (long long)(tiles + items_w));
         return SWA_EINVAL;
     }
@@ -316,11 +293,9 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     off = align256(off + (int64_t)sizeof(BImg) * n);
     const int64_t off_qs = off;
     off = align256(off + (int64_t)sizeof(BQuery) * (nq ? nq : 1));
-    const int64_t zero_off = off;                      // ticket, err, done[n], flags
+    const int64_t zero_off = off;                      // ticket, err, flags
     const int64_t off_ticket = off, off_err = off + 4;
-    const int64_t off_done = off + 256;
-    off = off_done + 4 * (int64_t)n;
-    const int64_t off_flags = align256(off);
+    const int64_t off_flags = off + 256;
     off = off_flags + 2 * 4 * tiles;
     const int64_t zero_bytes = off - zero_off;
     off = align256(off);
@@ -429,7 +404,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
             q.int_rn = q.n < (1ull << 32);
             q.div = rn::make_divisor(q.int_rn ? (uint32_t)q.n : 1u);
             q.img = pos;
-            q.nbx = (q.w.C + 255) / 256;
+            q.nbx = (q.w.C + kBWinPerBlock - 1) / kBWinPerBlock;
             q.item_base = item_base;
             q.nitems = (uint32_t)(q.w.R * q.nbx);
             item_base += q.nitems;
@@ -459,7 +434,6 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     a.total_items = item_base;
     a.ticket = reinterpret_cast<uint32_t *>(base + off_ticket);
     a.err = reinterpret_cast<uint32_t *>(base + off_err);
-    a.done = reinterpret_cast<uint32_t *>(base + off_done);
     *out = b;
     return SWA_OK;
 }
@@ -482,12 +456,16 @@ swa_status swa_batch_run(swa_batch *b, swa_stream stream)
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    const int64_t work = (int64_t)b->total_tiles + b->total_items;
-    int64_t blocks = std::min<int64_t>(sms, (work + kBatchWarps - 1) / kBatchWarps);
+    int64_t blocks = std::min<int64_t>(sms, ((int64_t)b->total_tiles + kBatchWarps - 1) /
+                                                kBatchWarps);
     if (blocks < 1) blocks = 1;
     {
-        LaunchScope ls("batch", s);
+        LaunchScope ls("batch_build", s);
         kern<<<(unsigned)blocks, kBatchWarps * 32, smem, s>>>(b->args);
+    }
+    if (b->total_items) {
+        LaunchScope ls("batch_windows", s);
+        k_batch_windows<<<b->total_items, 256, 0, s>>>(b->args.qs, b->args.nq, b->args.imgs);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -1,0 +1,278 @@
+"""Serving: a continuous-batching request loop over the C ABI.
+
+A request asks for window statistics (sum, mean, std) of one image for a
+list of windows.  The server
+
+- admits requests as they arrive, as long as a request slot and the device
+  memory budget allow (tables, build scratch, the staged image and the
+  outputs are all counted against the budget);
+- keeps built summed-area tables resident, keyed by image id, with
+  least-recently-used eviction of tables no in-flight request uses, so a
+  repeated query on the same image skips the upload and the rebuild (a
+  request that arrives while its image is still being built waits for that
+  build on the device instead of building again);
+- runs admitted requests on a small set of CUDA streams, so the builds and
+  queries of different requests overlap on the device;
+- records, per request, the time from arrival to completion.
+
+``plain_path`` runs the same requests the plain way for comparison: one at a
+time on one stream, uploading, building, querying and freeing the tables of
+every request.
+
+Results stay in device memory (tensors in ``Request.result``); a client copies
+them out when it needs them.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+import paper_2410_16291_gb300 as swa
+
+
+@dataclass
+class Request:
+    rid: int
+    image_id: object
+    host_image: object          # pinned host tensor (uint8 or int16 bit patterns)
+    windows: list               # [(wh, ww, sy, sx), ...]
+    arrival: float = 0.0        # seconds from the start of the run
+    result: list = None         # per window: {"sum", "mean", "std"} device tensors
+    admitted: float = None
+    done: float = None
+    hit: bool = False
+
+    @property
+    def latency(self):
+        return None if self.done is None else self.done - self.arrival
+
+
+@dataclass
+class _Entry:
+    sat: object                  # swa.SAT (anything with .free())
+    nbytes: int
+    ready: object = None         # torch.cuda.Event recorded after the build
+    refs: int = 0
+
+
+class TableCache:
+    """Resident tables keyed by image id under a byte budget.
+
+    ``used`` counts the cached tables plus whatever transient bytes callers
+    reserve; ``reserve`` evicts unreferenced tables, least recently used
+    first, until the request fits.
+    """
+
+    def __init__(self, budget_bytes: int):
+        self.budget = int(budget_bytes)
+        self.entries: "collections.OrderedDict[object, _Entry]" = collections.OrderedDict()
+        self.used = 0
+        self.evictions = 0
+
+    def get(self, key):
+        e = self.entries.get(key)
+        if e is not None:
+            self.entries.move_to_end(key)
+        return e
+
+    def reserve(self, need: int) -> bool:
+        if self.used + need <= self.budget:
+            self.used += need
+            return True
+        for key in list(self.entries.keys()):
+            e = self.entries[key]
+            if e.refs:
+                continue
+            del self.entries[key]
+            e.sat.free()
+            self.used -= e.nbytes
+            self.evictions += 1
+            if self.used + need <= self.budget:
+                self.used += need
+                return True
+        return False
+
+    def insert(self, key, entry: _Entry):
+        """Cache a built table whose bytes were already reserved."""
+        self.entries[key] = entry
+
+    def release(self, nbytes: int):
+        self.used -= nbytes
+
+    def clear(self):
+        for e in self.entries.values():
+            e.sat.free()
+        self.entries.clear()
+        self.used = 0
+
+
+def table_bytes(rows, cols, dtype_code):
+    """(resident table bytes, transient build scratch bytes) of one image."""
+    import ctypes
+    t, s = ctypes.c_int64(), ctypes.c_int64()
+    swa.check(swa.lib().swa_sat_bytes(rows, cols, dtype_code, swa.SWA_WITH_SQ, ctypes.byref(t),
+                                      ctypes.byref(s)), "swa_sat_bytes")
+    return t.value, s.value
+
+
+def output_bytes(rows, cols, windows):
+    n = 0
+    for wh, ww, sy, sx in windows:
+        R, C = swa.window_shape(rows, cols, wh, ww, sy, sx)
+        n += R * C
+    return 24 * n
+
+
+class Server:
+    """Continuous-batching server with a resident-table LRU cache.
+
+    budget_bytes: device memory the server may hold at once.
+    streams: number of CUDA streams requests are spread over.
+    slots: maximum number of requests on the device at once.
+    """
+
+    def __init__(self, budget_bytes: int, streams: int = 4, slots: int = 8,
+                 keep_results: bool = True):
+        import torch
+        self.keep_results = keep_results
+        self.torch = torch
+        self.budget = int(budget_bytes)
+        self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        self.slots = slots
+        self.cache = TableCache(budget_bytes)
+        self.inflight = []           # (request, event, transient_bytes, entry, image_tensor)
+        self.waiting = collections.deque()
+        self.completed = []
+        self.hits = 0
+        self.misses = 0
+        self._rr = 0
+
+    @property
+    def evictions(self):
+        return self.cache.evictions
+
+    # ----------------------------------------------------------- dispatch --
+    def _try_admit(self, req: Request, now: float) -> bool:
+        torch = self.torch
+        rows, cols = req.host_image.shape
+        code = swa._dtype_code(req.host_image)
+        out_b = output_bytes(rows, cols, req.windows)
+        entry = self.cache.get(req.image_id)
+        if entry is not None:
+            transient = out_b
+            if not self.cache.reserve(transient):
+                return False
+        else:
+            tab_b, scr_b = table_bytes(rows, cols, code)
+            img_b = rows * cols * req.host_image.element_size()
+            transient = out_b + scr_b + img_b
+            if tab_b + transient > self.budget:
+                raise MemoryError("request %d needs %d bytes, budget %d" %
+                                  (req.rid, tab_b + transient, self.budget))
+            if not self.cache.reserve(tab_b + transient):
+                return False
+        s = self.streams[self._rr % len(self.streams)]
+        self._rr += 1
+        img_dev = None
+        with torch.cuda.stream(s):
+            if entry is None:
+                img_dev = req.host_image.to("cuda", non_blocking=True)
+                sat = swa.build_sat(img_dev, with_sq=True, stream=s)
+                ready = torch.cuda.Event()
+                ready.record(s)
+                entry = _Entry(sat, tab_b, ready)
+                self.cache.insert(req.image_id, entry)
+                self.misses += 1
+            else:
+                s.wait_event(entry.ready)       # a build still in flight, or done
+                req.hit = True
+                self.hits += 1
+            entry.refs += 1
+            req.result = entry.sat.window_stats(req.windows, stream=s)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        req.admitted = now
+        self.inflight.append((req, ev, transient, entry, img_dev))
+        return True
+
+    def _poll(self, now: float):
+        still = []
+        for req, ev, transient, entry, img_dev in self.inflight:
+            if ev.query():
+                req.done = now
+                entry.refs -= 1
+                self.cache.release(transient)
+                if not self.keep_results:
+                    req.result = None
+                self.completed.append(req)
+            else:
+                still.append((req, ev, transient, entry, img_dev))
+        self.inflight = still
+
+    # -------------------------------------------------------------- run ---
+    def run(self, requests, realtime: bool = True, poll_s: float = 50e-6):
+        """Serve `requests` (sorted by arrival).  With realtime, a request
+        becomes visible at its arrival time; otherwise all arrive at once."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        t0 = time.perf_counter()
+        while pending or self.waiting or self.inflight:
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].arrival <= now):
+                r = pending.popleft()
+                if not realtime:
+                    r.arrival = now
+                self.waiting.append(r)
+            self._poll(now)
+            progressed = False
+            while self.waiting and len(self.inflight) < self.slots:
+                if not self._try_admit(self.waiting[0], now):
+                    break
+                self.waiting.popleft()
+                progressed = True
+            if not progressed:
+                nxt = pending[0].arrival - now if pending else poll_s
+                time.sleep(max(0.0, min(poll_s, nxt)))
+        self.torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.cache.clear()
+
+
+def plain_path(requests, realtime: bool = True, stream=None, keep_results: bool = True):
+    """The plain per-request path: in arrival order, one request at a time on
+    one stream, upload + build + query + free, waiting for each to finish."""
+    import torch
+    s = stream or torch.cuda.Stream()
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    t0 = time.perf_counter()
+    for r in reqs:
+        if realtime:
+            wait = r.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        else:
+            r.arrival = time.perf_counter() - t0
+        with torch.cuda.stream(s):
+            img = r.host_image.to("cuda", non_blocking=True)
+            sat = swa.build_sat(img, with_sq=True, stream=s)
+            r.result = sat.window_stats(r.windows, stream=s)
+            sat.free()
+        s.synchronize()
+        r.done = time.perf_counter() - t0
+        if not keep_results:
+            r.result = None
+    return time.perf_counter() - t0
+
+
+def latency_summary(requests):
+    lat = np.array([r.latency for r in requests if r.latency is not None])
+    if not len(lat):
+        return {}
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
+            "requests": int(len(lat))}
