@@ -488,39 +488,61 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
 #pragma unroll
         for (int k = 0; k < 8; ++k) { vs[k] += es + K_s; if (WQ) vq[k] += eq + K_q; }
     }
+    // Rows go in pairs: the two rows' prefix and warp-scan chains are
+    // independent, which gives the scheduler two chains to interleave.
     uint32_t cp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint64_t H_s = 0, H_q = 0;
     const int c1 = (int)(s * (kSliceCols / 16));
-    for (int r = 0; r < nr; ++r) {
-        uint32_t px[8];
-        smem8<T>(tile + r * kSliceCols, lane, px);
+    for (int r = 0; r < nr; r += 2) {
+        uint32_t pa[8], pb[8];
+        smem8<T>(tile + r * kSliceCols, lane, pa);
+        smem8<T>(tile + (r + 1) * kSliceCols, lane, pb);   // row r+1 < TH exists in the buffer
         uint64_t ls = lr_s[0], lq = lr_q[0];
 #pragma unroll
         for (int j = 1; j < RPL; ++j)
             if ((r >> 5) == j) { ls = lr_s[j]; lq = lr_q[j]; }
-        H_s += __shfl_sync(kFull, ls, r & 31);
-        if (WQ) H_q += __shfl_sync(kFull, lq, r & 31);
-        uint32_t lp[8];
-        QA lq8[8];
+        // r is even, so rows r and r+1 lie in the same group of 32.
+        const uint64_t ha_s = H_s + __shfl_sync(kFull, ls, r & 31);
+        const uint64_t hb_s = ha_s + __shfl_sync(kFull, ls, (r + 1) & 31);
+        uint64_t ha_q = 0, hb_q = 0;
+        if (WQ) {
+            ha_q = H_q + __shfl_sync(kFull, lq, r & 31);
+            hb_q = ha_q + __shfl_sync(kFull, lq, (r + 1) & 31);
+        }
+        H_s = hb_s;
+        H_q = hb_q;
+        uint32_t la[8], lb[8];
+        QA qa[8], qb[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            cp[k] += px[k];
-            lp[k] = cp[k] + (k ? lp[k - 1] : 0u);
+            cp[k] += pa[k];
+            la[k] = cp[k] + (k ? la[k - 1] : 0u);
+            cp[k] += pb[k];
+            lb[k] = cp[k] + (k ? lb[k - 1] : 0u);
             if (WQ) {
-                cqa[k] += (QA)px[k] * (QA)px[k];
-                lq8[k] = cqa[k] + (k ? lq8[k - 1] : (QA)0);
+                cqa[k] += (QA)pa[k] * (QA)pa[k];
+                qa[k] = cqa[k] + (k ? qa[k - 1] : (QA)0);
+                cqa[k] += (QA)pb[k] * (QA)pb[k];
+                qb[k] = cqa[k] + (k ? qb[k - 1] : (QA)0);
             }
         }
-        const uint32_t is = warp_incl_scan(lp[7], lane);
-        const uint64_t base_s = H_s + (uint64_t)(is - lp[7]);
-        uint64_t base_q = 0;
+        const uint32_t isa = warp_incl_scan(la[7], lane);
+        const uint32_t isb = warp_incl_scan(lb[7], lane);
+        const uint64_t base_as = ha_s + (uint64_t)(isa - la[7]);
+        const uint64_t base_bs = hb_s + (uint64_t)(isb - lb[7]);
+        uint64_t base_aq = 0, base_bq = 0;
         if (WQ) {
-            const QA iq = warp_incl_scan(lq8[7], lane);
-            base_q = H_q + (uint64_t)(iq - lq8[7]);
+            const QA iqa = warp_incl_scan(qa[7], lane);
+            const QA iqb = warp_incl_scan(qb[7], lane);
+            base_aq = ha_q + (uint64_t)(iqa - qa[7]);
+            base_bq = hb_q + (uint64_t)(iqb - qb[7]);
         }
-        emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_s, vs, lp, base_q, vq, lq8, a.tmS, a.tmQ, c1,
+        emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_as, vs, la, base_aq, vq, qa, a.tmS, a.tmQ, c1,
                          (int)(y0 + r), w.pol);
+        if (r + 1 < nr)
+            emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_bs, vs, lb, base_bq, vq, qb, a.tmS, a.tmQ,
+                             c1, (int)(y0 + r + 1), w.pol);
     }
     __syncwarp();     // the tile buffer is reused by the next ticket
     return true;

@@ -59,44 +59,72 @@ struct WinArgs {
     WinQ q[kQPerLaunch];
 };
 
-// Every block covers 256 consecutive windows of one output row of one query;
-// the query is found from the launch's block offsets (at most 16 entries).
+constexpr int kWinPerThread = 4;                  // windows per thread, 256 apart
+constexpr int kWinPerBlock = 256 * kWinPerThread;  // consecutive windows per block
+
+// Every block covers 1024 consecutive windows of one output row of one query
+// (thread t: windows t, t + 256, t + 512, t + 768 of the block, so every load
+// and store instruction stays coalesced); the query is found from the
+// launch's block offsets (at most 16 entries).  Block indices fit 32 bits.
 template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN>
 __global__ void __launch_bounds__(256) k_windows(const __grid_constant__ WinArgs a)
 {
+    const uint32_t bid = blockIdx.x;
     int k = 0;
 #pragma unroll 1
-    while (k + 1 < a.nq && (int64_t)blockIdx.x >= a.q[k + 1].first_block) ++k;
+    while (k + 1 < a.nq && bid >= (uint32_t)a.q[k + 1].first_block) ++k;
     const WinQ &q = a.q[k];
-    const int64_t blk = (int64_t)blockIdx.x - q.first_block;
-    const int64_t i = blk / q.nbx;
-    const int64_t j = (blk % q.nbx) * 256 + threadIdx.x;
-    if (j >= q.w.C) return;
-    const int64_t y0 = i * q.w.sy, x0 = j * q.w.sx;
-    const int64_t y1 = y0 + q.w.wh - 1, x1 = x0 + q.w.ww - 1;
+    const uint32_t blk = bid - (uint32_t)q.first_block;
+    const uint32_t nbx = (uint32_t)q.nbx;
+    const uint32_t i = blk / nbx;
+    const int64_t jb = (int64_t)(blk - i * nbx) * kWinPerBlock + threadIdx.x;
+    const int64_t y0 = (int64_t)i * q.w.sy, y1 = y0 + q.w.wh - 1;
     const int64_t ld = a.ld;
-    const bool top = y0 > 0, left = x0 > 0;
-    const int64_t rt = (y0 - 1) * ld, rb = y1 * ld;
-    uint64_t sw = __ldg(a.S + rb + x1);
-    if (top) sw -= __ldg(a.S + rt + x1);
-    if (left) sw -= __ldg(a.S + rb + x0 - 1);
-    if (top && left) sw += __ldg(a.S + rt + x0 - 1);
-    const int64_t o = i * q.w.out_ld + j;
-    if (DO_SUM) q.w.sum[o] = sw;
-    if (DO_MEAN)
-        q.w.mean[o] = INT_RN ? rn::mean_rn(sw, q.div) : __ddiv_rn(__ull2double_rn(sw), q.n_d);
-    if (DO_STD) {
-        uint64_t qw = __ldg(a.Q + rb + x1);
-        if (top) qw -= __ldg(a.Q + rt + x1);
-        if (left) qw -= __ldg(a.Q + rb + x0 - 1);
-        if (top && left) qw += __ldg(a.Q + rt + x0 - 1);
-        if (INT_RN) {
-            q.w.std[o] = rn::std_rn(q.n, sw, qw, q.div);
-        } else {
-            const unsigned __int128 D =
-                (unsigned __int128)q.n * qw - (unsigned __int128)sw * sw;
-            const double d = u128_to_double_rn((uint64_t)(D >> 64), (uint64_t)D);
-            q.w.std[o] = __ddiv_rn(__dsqrt_rn(d), q.n_d);
+    const bool top = y0 > 0;
+    const uint64_t *St = a.S + (y0 - 1) * ld, *Sb = a.S + y1 * ld;
+    const uint64_t *Qt = a.Q + (y0 - 1) * ld, *Qb = a.Q + y1 * ld;
+    const int64_t orow = (int64_t)i * q.w.out_ld;
+    // All corner loads of the thread's windows first (independent, so they
+    // are in flight together), then the arithmetic.
+    uint64_t sw[kWinPerThread], qw[kWinPerThread];
+#pragma unroll
+    for (int m = 0; m < kWinPerThread; ++m) {
+        const int64_t j = jb + 256 * m;
+        sw[m] = 0;
+        qw[m] = 0;
+        if (j < q.w.C) {
+            const int64_t x0 = j * q.w.sx, x1 = x0 + q.w.ww - 1;
+            const bool left = x0 > 0;
+            sw[m] = __ldg(Sb + x1);
+            if (top) sw[m] -= __ldg(St + x1);
+            if (left) sw[m] -= __ldg(Sb + x0 - 1);
+            if (top && left) sw[m] += __ldg(St + x0 - 1);
+            if (DO_STD) {
+                qw[m] = __ldg(Qb + x1);
+                if (top) qw[m] -= __ldg(Qt + x1);
+                if (left) qw[m] -= __ldg(Qb + x0 - 1);
+                if (top && left) qw[m] += __ldg(Qt + x0 - 1);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < kWinPerThread; ++m) {
+        const int64_t j = jb + 256 * m;
+        if (j >= q.w.C) break;
+        const int64_t o = orow + j;
+        if (DO_SUM) q.w.sum[o] = sw[m];
+        if (DO_MEAN)
+            q.w.mean[o] =
+                INT_RN ? rn::mean_rn(sw[m], q.div) : __ddiv_rn(__ull2double_rn(sw[m]), q.n_d);
+        if (DO_STD) {
+            if (INT_RN) {
+                q.w.std[o] = rn::std_rn(q.n, sw[m], qw[m], q.div);
+            } else {
+                const unsigned __int128 D =
+                    (unsigned __int128)q.n * qw[m] - (unsigned __int128)sw[m] * sw[m];
+                const double d = u128_to_double_rn((uint64_t)(D >> 64), (uint64_t)D);
+                q.w.std[o] = __ddiv_rn(__dsqrt_rn(d), q.n_d);
+            }
         }
     }
 }
@@ -157,7 +185,7 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
             const uint64_t area = (uint64_t)(w[k].wh * w[k].ww);
             if (done[k] || w[k].outputs != o || (area < (1ull << 32)) != int_rn) continue;
             done[k] = true;
-            const int64_t nbx = (w[k].C + 255) / 256;
+            const int64_t nbx = (w[k].C + kWinPerBlock - 1) / kWinPerBlock;
             if (w[k].R * nbx == 0) continue;
             WinQ &q = a.q[a.nq++];
             q.w = w[k];
