@@ -8,7 +8,9 @@ One step = one pass of the whole path over one image: build S and Q
 Default workload: the 70,000 x 85,000 uint8 synthetic microscopy image
 (5.95e9 px, 95 GB of tables) with windows 256 and 1024 at stride 16.
 ``--workload 1`` runs the 20,000 x 20,000 image with windows 50/100/200 at
-stride 1.
+stride 1; 3 the batched engine on 256 uneven images; 4 the served request
+stream; 5 the out-of-core banded path on a 70,000 x 85,000 uint16 image
+(host to host).
 
 Prints one JSON line.  ``value`` is image pixels per second of the whole step
 (Gpx/s) with the image resident in HBM; ``e2e`` is the same metric through
@@ -40,7 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--band-rows", type=int, default=5000,
+                    help="workload 5: rows per band (0: automatic)")
     ap.add_argument("--requests", type=int, default=200, help="workload 4: requests")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="workload 4: HBM budget")
     ap.add_argument("--plain-steps", type=int, default=2,
@@ -53,7 +57,9 @@ def parse():
                     help="rows of the CPU-baseline sample (0: sized to ~10 s)")
     ap.add_argument("--twopass", action="store_true", help="force the two-pass SAT build")
     ap.add_argument("--shape", default="",
-                    help="custom u8 image RxC (profiling cases), e.g. 8192x8192")
+                    help="custom image RxC (profiling cases), e.g. 8192x8192")
+    ap.add_argument("--dtype", default="u8", choices=["u8", "u16"],
+                    help="pixel type of a --shape image")
     ap.add_argument("--windows", default="",
                     help="custom windows w/stride list, e.g. 100/1,256/16")
     return ap.parse_args()
@@ -208,7 +214,8 @@ def cpu_baseline(im, windows, rows):
     import synth
 
     def rows_fn(n):
-        return synth.intensity_u8(n, im.cols, im.seed, synth.cluster_count(n, im.cols))
+        gen = synth.intensity_u16 if im.dtype == "u16" else synth.intensity_u8
+        return gen(n, im.cols, im.seed, synth.cluster_count(n, im.cols))
     if rows <= 0:
         probe = max(1024, max(w[0] for w in windows))
         px, _, dt = oracle_sample(rows_fn, im.cols, windows, probe)
@@ -235,14 +242,14 @@ def cpu_baseline(im, windows, rows):
 
 
 def workload_of(args):
-    """The benchmark image: a standard workload, or a custom u8 image for
-    profiling cases (--shape / --windows)."""
+    """The benchmark image: a standard workload, or a custom image for
+    profiling cases (--shape / --dtype / --windows)."""
     import synth
     if args.shape:
         r, c = (int(v) for v in args.shape.lower().split("x"))
         wins = [synth.Window(int(w), int(w), int(s), int(s)) for w, s in
                 (x.split("/") for x in (args.windows or "100/1").split(","))]
-        return synth.Image(r, c, "u8", "intensity", synth.DEFAULT_SEED + 17,
+        return synth.Image(r, c, args.dtype, "intensity", synth.DEFAULT_SEED + 17,
                            synth.cluster_count(r, c), wins)
     (im,) = synth.workload(args.workload)
     if args.windows:
@@ -263,7 +270,8 @@ def run_reference(args, rank, world):
     rows = max(rows, 1024)
 
     def rows_fn(n):
-        return synth.intensity_u8(n, im.cols, im.seed, synth.cluster_count(n, im.cols))
+        gen = synth.intensity_u16 if im.dtype == "u16" else synth.intensity_u8
+        return gen(n, im.cols, im.seed, synth.cluster_count(n, im.cols))
     for _ in range(args.warmup):
         oracle_sample(rows_fn, im.cols, windows, rows)
     tot_px, tot_out, tot_t = 0, 0, 0.0
@@ -293,7 +301,7 @@ def config_of(im, windows):
         "windows": ["%dx%d/s%d" % (w[0], w[1], w[2]) for w in windows],
         "outputs": "sum,mean,std", "tables": "S and Q, uint64",
         "l2": "inputs larger than L2 (image %.2f GB, tables %.1f GB)" % (
-            im.pixels / 1e9, 16 * im.pixels / 1e9)}
+            im.pixels * (2 if im.dtype == "u16" else 1) / 1e9, 16 * im.pixels / 1e9)}
 
 
 # ---------------------------------------------------------------- GPU legs --
@@ -313,8 +321,10 @@ def run_ours(args, rank, world, local_rank):
     im = workload_of(args)
     windows = [(w.wh, w.ww, w.sy, w.sx) for w in im.windows]
     px = im.pixels
-    host = torch.empty((im.rows, im.cols), dtype=torch.uint8, pin_memory=True)
-    im.generate(out=host.numpy())
+    u16 = im.dtype == "u16"
+    host = torch.empty((im.rows, im.cols), dtype=torch.int16 if u16 else torch.uint8,
+                       pin_memory=True)
+    im.generate(out=host.numpy().view(np.uint16) if u16 else host.numpy())
     dev = host.to("cuda", non_blocking=True)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
@@ -359,7 +369,7 @@ def run_ours(args, rank, world, local_rank):
     # Per-kernel averages and the dominant kernel's roofline.
     hbm, hbm_kind = peaks()
     tables = 2
-    build_bytes = px * (1 + 8 * tables)
+    build_bytes = px * ((2 if u16 else 1) + 8 * tables)
     kernels = {}
     for name, (n, tot, mx) in prof.items():
         kernels[name] = {"launches": n, "avg_ms": tot / n, "share": 0.0}
@@ -506,6 +516,23 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.synchronize()
     plain_ms = p0.elapsed_time(p1) / args.plain_steps
     plain_launches = (swa.lib().swa_launch_count() - l0) // args.plain_steps
+
+    # Per-kernel device time of both paths (event-bracketed launches, outside
+    # the graph): where each path spends its step.
+    def per_kernel(fn, reps):
+        swa.profile_begin()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return {k: {"launches": n // reps, "ms_per_pass": tot / reps}
+                for k, (n, tot, _) in swa.profile_end().items()}
+
+    def batch_pass():
+        with torch.cuda.stream(stream):
+            b.run(stream)
+    batch_kernels = per_kernel(batch_pass, max(1, args.plain_steps))
+    b.sync()
+    plain_kernels = per_kernel(plain_pass, max(1, args.plain_steps))
     hbm, hbm_kind = peaks()
     algo = sum(im.pixels * ((2 if im.dtype == "u16" else 1) + 16) for im in imgs) + 24 * n_out
     if rank != 0:
@@ -521,8 +548,9 @@ def run_batch(args, rank, world, local_rank):
                                                       "replayed as one CUDA graph",
                        "l2": "inputs larger than L2 (%.1f GB of tables)" % (16 * px / 1e9)},
             "window_outputs_per_s": world * n_out / (ms / 1e3),
+            "kernels": batch_kernels,
             "plain_path": {"ms_per_pass": plain_ms, "gpx_s": px / (plain_ms / 1e3) / 1e9,
-                           "launches_per_pass": plain_launches},
+                           "launches_per_pass": plain_launches, "kernels": plain_kernels},
             "speedup_vs_plain": plain_ms / ms,
             "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": algo / (ms / 1e3) / 1e9,
                          "peak": hbm, "unit": "GB/s", "frac": algo / (ms / 1e3) / 1e9 / hbm,
@@ -544,6 +572,7 @@ def run_serve(args, rank, world, local_rank):
 
     import synth
     from paper_2410_16291_gb300 import build as swa_build
+    import paper_2410_16291_gb300 as swa
     from paper_2410_16291_gb300 import serve
     swa_build.build()
     torch.cuda.set_device(local_rank)
@@ -567,39 +596,184 @@ def run_serve(args, rank, world, local_rank):
     px = sum(pool[idx].pixels for _, idx, _ in trace)
     n_out = sum(((pool[idx].rows - w.wh) // w.sy + 1) * ((pool[idx].cols - w.ww) // w.sx + 1)
                 for _, idx, wl in trace for w in wl)
-    # warm-up: one small request through each path
-    small = min(host, key=lambda k: pool[k].pixels)
-    warm = [serve.Request(-1, small, host[small], [(16, 16, 4, 4)])]
-    sv = serve.Server(int(args.budget_gb * 1e9), streams=4, slots=8, keep_results=False)
-    sv.run(warm, realtime=False)
-    serve.plain_path([serve.Request(-2, small, host[small], [(16, 16, 4, 4)])], realtime=False)
-    sv.cache.clear()
-    reqs = requests()
-    t_srv = sv.run(reqs, realtime=True)
-    srv = serve.latency_summary(reqs)
-    hits, misses, evictions = sv.hits, sv.misses, sv.evictions
-    sv.close()
-    torch.cuda.synchronize()
-    preqs = requests()
-    t_plain = serve.plain_path(preqs, realtime=True, keep_results=False)
-    plain = serve.latency_summary(preqs)
-    n = len(reqs)
-    line = {"metric": METRIC, "value": px / t_srv / 1e9, "unit": "Gpx/s", "n_gpus": 1,
-            "steps": n, "warmup": 1, "ms_per_step": t_srv / n * 1e3,
+    # Both paths run on streams created once, as a long-lived server's would
+    # be; one untimed closed-loop pass of each first, so that PyTorch's
+    # caching allocator (which keeps freed device blocks per stream) and the
+    # library's memory pool already hold blocks for the staged images and
+    # tables, as they do in steady state.
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    plain_stream = torch.cuda.Stream()
+
+    def served(realtime):
+        srv = serve.Server(int(args.budget_gb * 1e9), streams=streams, slots=8,
+                           keep_results=False)
+        reqs = requests()
+        l0 = swa.lib().swa_launch_count()
+        t = srv.run(reqs, realtime=realtime)
+        out = dict(serve.latency_summary(reqs), seconds=t, requests_per_s=len(reqs) / t,
+                   window_outputs_per_s=n_out / t, cache_hits=srv.hits,
+                   cache_misses=srv.misses, evictions=srv.evictions,
+                   gpu_launches=swa.lib().swa_launch_count() - l0)
+        srv.close()
+        torch.cuda.synchronize()
+        return t, out
+
+    def plain(realtime):
+        reqs = requests()
+        t = serve.plain_path(reqs, realtime=realtime, stream=plain_stream, keep_results=False)
+        torch.cuda.synchronize()
+        return t, dict(serve.latency_summary(reqs), seconds=t, requests_per_s=len(reqs) / t,
+                       window_outputs_per_s=n_out / t)
+    served(False)
+    plain(False)
+    # closed loop (every request submitted at t=0): throughput
+    t_srv_c, srv_c = served(False)
+    t_plain_c, plain_c = plain(False)
+    # open loop (Poisson arrivals in real time): latency
+    t_srv, srv = served(True)
+    t_plain, plain_rt = plain(True)
+    n = len(trace)
+    line = {"metric": METRIC, "value": px / t_srv_c / 1e9, "unit": "Gpx/s", "n_gpus": 1,
+            "steps": n, "warmup": 1, "ms_per_step": t_srv_c / n * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": "served: Poisson 200 req/s over 64 images (sides "
                                    "1,000-40,000, uint8/uint16), 1-8 windows 16-1024 px, "
                                    "stride 4-16, sum/mean/std",
                        "requests": n, "budget_gb": args.budget_gb, "streams": 4, "slots": 8,
-                       "image_pixels_requested": px, "window_outputs": n_out},
-            "served": dict(srv, seconds=t_srv, requests_per_s=n / t_srv,
-                           window_outputs_per_s=n_out / t_srv, cache_hits=hits,
-                           cache_misses=misses, evictions=evictions),
-            "plain_path": dict(plain, seconds=t_plain, requests_per_s=n / t_plain,
-                               window_outputs_per_s=n_out / t_plain),
-            "throughput_vs_plain": t_plain / t_srv, "host_generation_s": gen_s,
-            "window_outputs_per_s": n_out / t_srv, "cpu_baseline": None, "e2e": None}
+                       "image_pixels_requested": px, "window_outputs": n_out,
+                       "value": "closed loop: requested image pixels / makespan with "
+                                "every request submitted at once"},
+            "served_closed_loop": srv_c, "plain_closed_loop": plain_c,
+            "served_realtime": srv, "plain_realtime": plain_rt,
+            "throughput_vs_plain": t_plain_c / t_srv_c,
+            "p99_vs_plain_realtime": (plain_rt.get("p99_ms", 0) / srv["p99_ms"]
+                                      if srv.get("p99_ms") else None),
+            "host_generation_s": gen_s,
+            "window_outputs_per_s": n_out / t_srv_c, "gpu_launches": srv_c["gpu_launches"],
+            "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
+def run_banded(args, rank, world, local_rank):
+    """Workload 5: the 70,000 x 85,000 uint16 image (whose whole squared
+    table could overflow uint64) through swa_analyze_banded, pinned host
+    image in and host outputs out, windows 256 and 1024 at stride 16.  Every
+    step moves the image over the host link, so value and e2e coincide; the
+    link's bound is a plain pinned host-to-device copy of the image timed in
+    the same run."""
+    import torch
+
+    import paper_2410_16291_gb300 as swa
+    import synth
+    from paper_2410_16291_gb300 import build as swa_build
+    swa_build.build()
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+    r, c = 70000, 85000
+    t0 = time.perf_counter()
+    host = torch.empty((r, c), dtype=torch.int16, pin_memory=True)
+    synth.intensity_u16(r, c, synth.DEFAULT_SEED + 5, 50000, out=host.numpy().view(np.uint16))
+    gen_s = time.perf_counter() - t0
+    windows = [(256, 256, 16, 16), (1024, 1024, 16, 16)]
+    shapes = [swa.window_shape(r, c, *w) for w in windows]
+    outs = [{"sum": torch.empty(sh, dtype=torch.int64, pin_memory=True),
+             "mean": torch.empty(sh, dtype=torch.float64, pin_memory=True),
+             "std": torch.empty(sh, dtype=torch.float64, pin_memory=True)} for sh in shapes]
+    n_out = sum(R * C for R, C in shapes)
+    px = r * c
+    stream = torch.cuda.current_stream()
+
+    def step():
+        swa.analyze(host, windows, out=outs, stream=stream, band_rows=args.band_rows)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(gpu_id_for_smi(local_rank))
+    if rank == 0:
+        clocks.start()
+    if dist:
+        td.barrier()
+    l0 = swa.lib().swa_launch_count()
+    swa.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = swa.profile_end()
+    launches = swa.lib().swa_launch_count() - l0
+    if dist:
+        td.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device="cuda")
+    clk = clocks.stop() if rank == 0 else None
+    # The host link alone: the best of three pinned copies of the whole
+    # image, device-timed.
+    dev = torch.empty((r, c), dtype=torch.int16, device="cuda")
+    dev.copy_(host, non_blocking=True)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(3):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        dev.copy_(host, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, c0.elapsed_time(c1))
+    h2d_gbs = host.numel() * 2 / (best / 1e3) / 1e9
+    del dev
+    # Bytes over the link per step: every band's rows (halo included) in,
+    # every output out.
+    B = args.band_rows
+    halo_rows = 0 if B else None       # the library picks B itself when 0
+    if B:
+        for b in range(1, -(-r // B)):
+            tops = []
+            for wh, _, sy, _ in windows:
+                ib, ie = swa.band_range(r, wh, sy, B, b)
+                if ib < ie:
+                    tops.append(ib * sy)
+            halo_rows += b * B - min(tops) if tops else 0
+    h2d = (r + (halo_rows or 0)) * c * 2
+    d2h = 24 * n_out
+    hbm, hbm_kind = peaks()
+    kernels = {k: {"launches": n, "avg_ms": tot / n, "share": tot / max(1e-9, sum(
+        t for _, t, _ in prof.values()))} for k, (n, tot, _) in prof.items()}
+    build = kernels.get("sat_build", {"avg_ms": float("nan"), "launches": 0})
+    band_px = (r + (halo_rows or 0)) * c / max(1, build["launches"] // args.steps)
+    build_bytes = band_px * (2 + 16)
+    if rank != 0:
+        return
+    value = job_throughput(px, ms / 1e3, world) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "Gpx/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "70000x85000 u16 synthetic microscopy image, 50000 clusters, "
+                                   "out-of-core banded analysis, pinned host image in, host "
+                                   "outputs out",
+                       "windows": ["256x256/s16", "1024x1024/s16"], "outputs": "sum,mean,std",
+                       "band_rows": B, "halo_rows_per_step": halo_rows,
+                       "l2": "inputs larger than L2 (image 11.9 GB)"},
+            "window_outputs_per_s": world * n_out / (ms / 1e3),
+            "kernels": kernels,
+            "host_link": {"h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                          "achieved_gbs": (h2d + d2h) / (ms / 1e3) / 1e9,
+                          "pinned_h2d_copy_gbs": h2d_gbs,
+                          "frac": (h2d + d2h) / (ms / 1e3) / 1e9 / h2d_gbs},
+            "roofline": {"bound": "hbm", "kernel": "sat_build",
+                         "achieved": build_bytes / (build["avg_ms"] / 1e3) / 1e9,
+                         "peak": hbm, "unit": "GB/s",
+                         "frac": build_bytes / (build["avg_ms"] / 1e3) / 1e9 / hbm,
+                         "peak_kind": hbm_kind, "algorithmic_bytes_per_launch": build_bytes,
+                         "traffic": None},
+            "cpu_baseline": None,
+            "e2e": {"value": value, "unit": "Gpx/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "host_generation_s": gen_s, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -620,6 +794,8 @@ def main():
         run_batch(args, rank, world, local_rank)
     elif args.workload == 4:
         run_serve(args, rank, world, local_rank)
+    elif args.workload == 5:
+        run_banded(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

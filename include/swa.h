@@ -202,6 +202,49 @@ swa_status swa_analyze(const void *image, int64_t rows, int64_t cols,
                        const swa_window *windows, int32_t n, swa_stream stream);
 
 /*
+ * Out-of-core analysis in row bands: the results of swa_analyze for images
+ * whose tables do not fit in device memory, or whose squared-pixel table
+ * would overflow uint64 as a whole (a uint16 image of more than
+ * 4,295,098,370 pixels).  It rests on the corner lookup of Section II-B: a
+ * window's sum is the difference of table rows y0-1 and y1, and a table
+ * built from image row L instead of row 0 changes both rows by the same
+ * column sums, so every window whose top row is at or below L still comes
+ * out exact.  The call walks the image in bands of `band_rows` rows: band b
+ * serves the windows whose BOTTOM row lies in [b*band_rows,
+ * min((b+1)*band_rows, rows)) (swa_band_range), builds the tables of image
+ * rows [L_b, min((b+1)*band_rows, rows)), L_b being the top row of the
+ * band's first window over all queries (at most max(wh)-1 rows above the
+ * band), evaluates the band's output rows into place, and reuses the table
+ * buffers for the next band.  Device memory is about (band_rows + max wh)
+ * rows of image and tables plus two bands of outputs, independent of `rows`.
+ * Tables are not returned.  Image bands are uploaded and results downloaded
+ * on an internal second stream, overlapping the work of the neighbouring
+ * band; the call returns after every result is in place.
+ *
+ * image, pitch_bytes, dtype, windows, n, stream: as swa_analyze (the image
+ * and every output may be host or device memory; pinned host memory gives
+ * full-speed copies).  band_rows: rows per band, >= 1; 0 picks it so one
+ * band's tables take about 8 GiB (lowered if needed to satisfy the bound
+ * below).  The overflow bound applies per band, to (band_rows + max wh - 1)
+ * rows; a window's sum is exact whenever it is below 2^64 itself.
+ * Errors: as swa_analyze; SWA_EOVERFLOW if the given band_rows (or, with 0,
+ * even one row plus the halo) could overflow a table entry.
+ * No counterpart in the paper, which keeps whole tables in memory.
+ */
+swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols,
+                              int64_t pitch_bytes, swa_dtype dtype,
+                              const swa_window *windows, int32_t n,
+                              int64_t band_rows, swa_stream stream);
+
+/* The band partition of swa_analyze_banded for one query (host only): output
+ * rows [*i_begin, *i_end) are the windows whose bottom row i*sy + wh - 1
+ * lies in [b*band_rows, min((b+1)*band_rows, rows)); empty (both = R) for b
+ * past the last band.  SWA_EINVAL for non-positive sizes, wh > rows or
+ * b < 0. */
+swa_status swa_band_range(int64_t rows, int64_t wh, int64_t sy, int64_t band_rows,
+                          int64_t b, int64_t *i_begin, int64_t *i_end);
+
+/*
  * Batched engine: many images of uneven sizes and dtypes, each with its own
  * window queries.  A run is one persistent launch that builds the tables of
  * every image (the single-pass build, all images' tiles in one work queue),

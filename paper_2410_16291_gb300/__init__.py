@@ -63,6 +63,9 @@ SIGNATURES = {
     "swa_sync": (ctypes.c_int, [_VP]),
     "swa_free": (None, [_VP]),
     "swa_analyze": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _P(swa_window), _I32, _VP]),
+    "swa_analyze_banded": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _P(swa_window), _I32,
+                                          _I64, _VP]),
+    "swa_band_range": (ctypes.c_int, [_I64, _I64, _I64, _I64, _I64, _P(_I64), _P(_I64)]),
     "swa_set_memory_limit": (ctypes.c_int, [_I64]),
     "swa_memory_in_use": (_I64, []),
     "swa_trim": (ctypes.c_int, [_I64]),
@@ -267,10 +270,14 @@ def build_sat(image, with_sq=True, twopass=False, stream=None) -> SAT:
     return SAT(h.value, rows, cols, with_sq, stream)
 
 
-def analyze(image, windows, outputs=("sum", "mean", "std"), out=None, stream=None):
+def analyze(image, windows, outputs=("sum", "mean", "std"), out=None, stream=None,
+            band_rows=None):
     """One request end to end through ``swa_analyze``: image and outputs may
     live in host (ideally pinned) or device memory.  Returns the output dicts
-    (allocated like the image when ``out`` is None)."""
+    (allocated like the image when ``out`` is None).  With ``band_rows`` (0
+    for automatic) the request goes through ``swa_analyze_banded`` instead:
+    tables are built band by band, for images whose tables exceed device
+    memory or the uint64 bound."""
     import torch
     rows, cols = image.shape
     mask = (SWA_OUT_SUM if "sum" in outputs else 0) | (
@@ -296,10 +303,25 @@ def analyze(image, windows, outputs=("sum", "mean", "std"), out=None, stream=Non
                             o["mean"].data_ptr() if "mean" in o else None,
                             o["std"].data_ptr() if "std" in o else None, ld)
         res.append(o)
-    check(lib().swa_analyze(image.data_ptr(), rows, cols, image.stride(0) * image.element_size(),
-                            _dtype_code(image), arr, len(windows), _stream_ptr(stream)),
-          "swa_analyze")
+    if band_rows is None:
+        check(lib().swa_analyze(image.data_ptr(), rows, cols,
+                                image.stride(0) * image.element_size(), _dtype_code(image), arr,
+                                len(windows), _stream_ptr(stream)), "swa_analyze")
+    else:
+        check(lib().swa_analyze_banded(image.data_ptr(), rows, cols,
+                                       image.stride(0) * image.element_size(),
+                                       _dtype_code(image), arr, len(windows), int(band_rows),
+                                       _stream_ptr(stream)), "swa_analyze_banded")
     return res
+
+
+def band_range(rows, wh, sy, band_rows, b):
+    """Output rows [i_begin, i_end) that band b of swa_analyze_banded serves
+    (host only)."""
+    ib, ie = _I64(), _I64()
+    check(lib().swa_band_range(rows, wh, sy, band_rows, b, ctypes.byref(ib), ctypes.byref(ie)),
+          "swa_band_range")
+    return ib.value, ie.value
 
 
 class Batch:

@@ -29,12 +29,6 @@ std::atomic<uint32_t> g_hooks{0};
 std::unordered_set<Handle *> g_live;
 thread_local char t_err[512];
 
-swa_status cuda_fail(cudaError_t e, const char *what)
-{
-    set_error("%s: %s", what, cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? SWA_ENOMEM : SWA_ECUDA;
-}
-
 // The library's stream-ordered pool on the current device.  It keeps freed
 // memory cached (release threshold = max) so a rebuild of the same size does
 // not map new pages; swa_trim hands it back.
@@ -58,18 +52,6 @@ cudaError_t pool_for(int dev, cudaMemPool_t *out)
     }
     *out = g_pool[dev];
     return cudaSuccess;
-}
-
-int64_t pixel_bytes(int dtype) { return dtype == SWA_U8 ? 1 : 2; }
-
-bool fits_u64(int64_t rows, int64_t cols, int dtype, bool with_q)
-{
-    const unsigned __int128 n = (unsigned __int128)rows * (unsigned __int128)cols;
-    const unsigned __int128 mx = dtype == SWA_U8 ? 255 : 65535;
-    const unsigned __int128 lim = (unsigned __int128)1 << 64;
-    if (n * mx >= lim) return false;
-    if (with_q && n * mx * mx >= lim) return false;
-    return true;
 }
 
 bool live(const swa_sat *h)
@@ -112,6 +94,7 @@ swa_status check_window(const Handle *h, const swa_window &w, WinDesc *d)
         return SWA_EINVAL;
     }
     d->out_ld = w.out_ld;
+    d->row0 = 0;
     d->outputs = o;
     d->sum = w.sum;
     d->mean = w.mean;
@@ -141,6 +124,24 @@ swa_status run_windows(const Handle *h, const WinDesc *d, int n, cudaStream_t s)
 }
 
 }  // namespace
+
+swa_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SWA_ENOMEM : SWA_ECUDA;
+}
+
+int64_t pixel_bytes(int dtype) { return dtype == SWA_U8 ? 1 : 2; }
+
+bool fits_u64(int64_t rows, int64_t cols, int dtype, bool with_q)
+{
+    const unsigned __int128 n = (unsigned __int128)rows * (unsigned __int128)cols;
+    const unsigned __int128 mx = dtype == SWA_U8 ? 255 : 65535;
+    const unsigned __int128 lim = (unsigned __int128)1 << 64;
+    if (n * mx >= lim) return false;
+    if (with_q && n * mx * mx >= lim) return false;
+    return true;
+}
 
 void set_error(const char *fmt, ...)
 {

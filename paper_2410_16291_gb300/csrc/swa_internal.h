@@ -66,6 +66,12 @@ class LaunchScope {
 };
 void set_error(const char *fmt, ...);
 uint32_t test_hooks();
+// Records the CUDA error; SWA_ENOMEM for allocation failures, else SWA_ECUDA.
+swa_status cuda_fail(cudaError_t e, const char *what);
+int64_t pixel_bytes(int dtype);
+// Overflow guard: every entry of S (and of Q with with_q) of a rows x cols
+// image of this dtype is below 2^64 even for an all-maximum image.
+bool fits_u64(int64_t rows, int64_t cols, int dtype, bool with_q);
 
 // SAT build (sat_build.cu).
 BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype,
@@ -74,8 +80,14 @@ swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S,
                         uint64_t *Q, char *scratch, uint32_t *err, cudaStream_t s);
 
 // Window statistics (window_stats.cu).
+// One window query: output (i, j) is the window whose top-left pixel is at
+// table row row0 + i*sy, column j*sx.  row0 > 0 serves a table that starts
+// above the first window (a band of a larger image): corner rows above the
+// table's first row read as 0, which is exact when the table starts at or
+// above every window's top row.
 struct WinDesc {
     int64_t wh, ww, sy, sx, R, C, out_ld;
+    int64_t row0;
     uint32_t outputs;
     uint64_t *sum;
     double *mean, *std;

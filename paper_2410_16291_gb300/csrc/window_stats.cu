@@ -59,16 +59,22 @@ struct WinArgs {
     WinQ q[kQPerLaunch];
 };
 
-constexpr int kWinPerThread = 4;                  // windows per thread, 256 apart
-constexpr int kWinPerBlock = 256 * kWinPerThread;  // consecutive windows per block
+// Windows per thread: 4 (256 apart) where the arithmetic dominates, i.e.
+// dense column strides whose corner loads mostly hit the same sectors; 1
+// where the gather dominates (column stride >= kSparseStride: every corner
+// load touches its own sector, and more resident warps hide more latency).
+constexpr int kSparseStride = 4;
+inline int wins_per_thread(int64_t sx) { return sx >= kSparseStride ? 1 : 4; }
 
-// Every block covers 1024 consecutive windows of one output row of one query
-// (thread t: windows t, t + 256, t + 512, t + 768 of the block, so every load
-// and store instruction stays coalesced); the query is found from the
-// launch's block offsets (at most 16 entries).  Block indices fit 32 bits.
-template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN>
+// Every block covers 256*WPT consecutive windows of one output row of one
+// query (thread t: windows t, t + 256, ... of the block, so every load and
+// store instruction stays coalesced); the query is found from the launch's
+// block offsets (at most 16 entries).  Block indices fit 32 bits.
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN, int WPT>
 __global__ void __launch_bounds__(256) k_windows(const __grid_constant__ WinArgs a)
 {
+    constexpr int kWinPerThread = WPT;
+    constexpr int kWinPerBlock = 256 * WPT;
     const uint32_t bid = blockIdx.x;
     int k = 0;
 #pragma unroll 1
@@ -78,7 +84,7 @@ __global__ void __launch_bounds__(256) k_windows(const __grid_constant__ WinArgs
     const uint32_t nbx = (uint32_t)q.nbx;
     const uint32_t i = blk / nbx;
     const int64_t jb = (int64_t)(blk - i * nbx) * kWinPerBlock + threadIdx.x;
-    const int64_t y0 = (int64_t)i * q.w.sy, y1 = y0 + q.w.wh - 1;
+    const int64_t y0 = q.w.row0 + (int64_t)i * q.w.sy, y1 = y0 + q.w.wh - 1;
     const int64_t ld = a.ld;
     const bool top = y0 > 0;
     const uint64_t *St = a.S + (y0 - 1) * ld, *Sb = a.S + y1 * ld;
@@ -130,13 +136,14 @@ __global__ void __launch_bounds__(256) k_windows(const __grid_constant__ WinArgs
 }
 
 template <bool A, bool B, bool C, bool I>
-void launch_one(const WinArgs &a, unsigned blocks, cudaStream_t s)
+void launch_one(const WinArgs &a, unsigned blocks, int wpt, cudaStream_t s)
 {
     LaunchScope ls("window_stats", s);
-    k_windows<A, B, C, I><<<blocks, 256, 0, s>>>(a);
+    if (wpt == 1) k_windows<A, B, C, I, 1><<<blocks, 256, 0, s>>>(a);
+    else k_windows<A, B, C, I, 4><<<blocks, 256, 0, s>>>(a);
 }
 
-swa_status flush(WinArgs &a, int64_t blocks, uint32_t o, bool int_rn, cudaStream_t s)
+swa_status flush(WinArgs &a, int64_t blocks, uint32_t o, bool int_rn, int wpt, cudaStream_t s)
 {
     if (a.nq == 0 || blocks == 0) return SWA_OK;
     if (blocks > 0x7fffffffLL) {
@@ -146,7 +153,7 @@ swa_status flush(WinArgs &a, int64_t blocks, uint32_t o, bool int_rn, cudaStream
     const bool ds = o & SWA_OUT_SUM, dm = o & SWA_OUT_MEAN, dd = o & SWA_OUT_STD;
     const unsigned nb = (unsigned)blocks;
 #define SWA_L(A, B, C)                                                   \
-    (int_rn ? launch_one<A, B, C, true>(a, nb, s) : launch_one<A, B, C, false>(a, nb, s))
+    (int_rn ? launch_one<A, B, C, true>(a, nb, wpt, s) : launch_one<A, B, C, false>(a, nb, wpt, s))
     if (ds && dm && dd) SWA_L(true, true, true);
     else if (ds && dm) SWA_L(true, true, false);
     else if (ds && dd) SWA_L(true, false, true);
@@ -165,8 +172,9 @@ swa_status flush(WinArgs &a, int64_t blocks, uint32_t o, bool int_rn, cudaStream
 
 }  // namespace
 
-// Queries sharing an output selection and arithmetic path go into one launch
-// (up to 16 per launch); the others follow in launches of their own.
+// Queries sharing an output selection, arithmetic path and windows per
+// thread go into one launch (up to 16 per launch); the others follow in
+// launches of their own.
 swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, const WinDesc *w,
                           int n, cudaStream_t s)
 {
@@ -175,6 +183,7 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
         if (done[k0]) continue;
         const uint32_t o = w[k0].outputs;
         const bool int_rn = (uint64_t)(w[k0].wh * w[k0].ww) < (1ull << 32);
+        const int wpt = wins_per_thread(w[k0].sx);
         WinArgs a;
         a.S = S;
         a.Q = Q;
@@ -183,9 +192,11 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
         int64_t blocks = 0;
         for (int k = k0; k < n; ++k) {
             const uint64_t area = (uint64_t)(w[k].wh * w[k].ww);
-            if (done[k] || w[k].outputs != o || (area < (1ull << 32)) != int_rn) continue;
+            if (done[k] || w[k].outputs != o || (area < (1ull << 32)) != int_rn ||
+                wins_per_thread(w[k].sx) != wpt)
+                continue;
             done[k] = true;
-            const int64_t nbx = (w[k].C + kWinPerBlock - 1) / kWinPerBlock;
+            const int64_t nbx = (w[k].C + 256 * wpt - 1) / (256 * wpt);
             if (w[k].R * nbx == 0) continue;
             WinQ &q = a.q[a.nq++];
             q.w = w[k];
@@ -196,13 +207,13 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
             q.first_block = blocks;
             blocks += w[k].R * nbx;
             if (a.nq == kQPerLaunch) {
-                swa_status st = flush(a, blocks, o, int_rn, s);
+                swa_status st = flush(a, blocks, o, int_rn, wpt, s);
                 if (st != SWA_OK) return st;
                 a.nq = 0;
                 blocks = 0;
             }
         }
-        swa_status st = flush(a, blocks, o, int_rn, s);
+        swa_status st = flush(a, blocks, o, int_rn, wpt, s);
         if (st != SWA_OK) return st;
     }
     return SWA_OK;

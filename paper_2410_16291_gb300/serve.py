@@ -5,7 +5,8 @@ list of windows.  The server
 
 - admits requests as they arrive, as long as a request slot and the device
   memory budget allow (tables, build scratch, the staged image and the
-  outputs are all counted against the budget);
+  outputs are all counted against the budget); a request that fits may go
+  ahead of an older one that does not, a bounded number of times;
 - keeps built summed-area tables resident, keyed by image id, with
   least-recently-used eviction of tables no in-flight request uses, so a
   repeated query on the same image skips the upload and the rebuild (a
@@ -44,6 +45,7 @@ class Request:
     admitted: float = None
     done: float = None
     hit: bool = False
+    bypassed: int = 0            # younger requests admitted while this one waited
 
     @property
     def latency(self):
@@ -79,9 +81,14 @@ class TableCache:
         return e
 
     def reserve(self, need: int) -> bool:
+        """Reserve ``need`` bytes, evicting only if that makes them fit: a
+        reservation that fails evicts nothing."""
         if self.used + need <= self.budget:
             self.used += need
             return True
+        freeable = sum(e.nbytes for e in self.entries.values() if not e.refs)
+        if self.used - freeable + need > self.budget:
+            return False
         for key in list(self.entries.keys()):
             e = self.entries[key]
             if e.refs:
@@ -130,18 +137,28 @@ class Server:
     """Continuous-batching server with a resident-table LRU cache.
 
     budget_bytes: device memory the server may hold at once.
-    streams: number of CUDA streams requests are spread over.
+    streams: number of CUDA streams requests are spread over, or a list of
+    existing torch.cuda.Stream objects to use (a long-lived server reuses
+    its streams, and with them the device blocks PyTorch's caching allocator
+    keeps per stream).
     slots: maximum number of requests on the device at once.
+    lookahead, max_bypass: admission may skip over a request that does not
+    fit yet (see ``_admit``).
     """
 
     def __init__(self, budget_bytes: int, streams: int = 4, slots: int = 8,
-                 keep_results: bool = True):
+                 keep_results: bool = True, lookahead: int = 8, max_bypass: int = 16):
         import torch
         self.keep_results = keep_results
         self.torch = torch
         self.budget = int(budget_bytes)
-        self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        if isinstance(streams, int):
+            self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        else:
+            self.streams = list(streams)
         self.slots = slots
+        self.lookahead = lookahead
+        self.max_bypass = max_bypass
         self.cache = TableCache(budget_bytes)
         self.inflight = []           # (request, event, transient_bytes, entry, image_tensor)
         self.waiting = collections.deque()
@@ -212,6 +229,34 @@ class Server:
                 still.append((req, ev, transient, entry, img_dev))
         self.inflight = still
 
+    def _admit(self, now: float) -> bool:
+        """Admit waiting requests in arrival order while slots and memory
+        allow.  When the oldest request does not fit, up to ``lookahead``
+        younger ones that do fit (typically cache hits, which need only
+        output memory) go ahead of it; each bypass is counted on the oldest
+        request, and after ``max_bypass`` of them nothing may overtake it,
+        so a large miss is delayed but never starved."""
+        progressed = False
+        while self.waiting and len(self.inflight) < self.slots:
+            head = self.waiting[0]
+            if self._try_admit(head, now):
+                self.waiting.popleft()
+                progressed = True
+                continue
+            if head.bypassed >= self.max_bypass:
+                break
+            admitted = None
+            for i in range(1, min(len(self.waiting), 1 + self.lookahead)):
+                if self._try_admit(self.waiting[i], now):
+                    admitted = i
+                    break
+            if admitted is None:
+                break
+            del self.waiting[admitted]
+            head.bypassed += 1
+            progressed = True
+        return progressed
+
     # -------------------------------------------------------------- run ---
     def run(self, requests, realtime: bool = True, poll_s: float = 50e-6):
         """Serve `requests` (sorted by arrival).  With realtime, a request
@@ -226,12 +271,7 @@ class Server:
                     r.arrival = now
                 self.waiting.append(r)
             self._poll(now)
-            progressed = False
-            while self.waiting and len(self.inflight) < self.slots:
-                if not self._try_admit(self.waiting[0], now):
-                    break
-                self.waiting.popleft()
-                progressed = True
+            progressed = self._admit(now)
             if not progressed:
                 nxt = pending[0].arrival - now if pending else poll_s
                 time.sleep(max(0.0, min(poll_s, nxt)))

@@ -114,3 +114,33 @@ def test_u16_all_max_at_the_overflow_edge():
     assert f64(o["std"])[0, 0] == 0.0 and f64(o["mean"])[0, 0] == float(v)
     del S, Q, dev
     sat.free()
+
+
+def test_u16_70k_by_85k_banded():
+    """70,000 x 85,000 uint16 (5.95e9 px): the squared-pixel table of the
+    whole image could overflow uint64, so the one-table path refuses it; the
+    banded path (pinned host image in, host outputs out, 5,000-row bands)
+    gives every sampled window equal to the definition, with extra samples
+    on windows that end just past a band edge (their tables start in the
+    band above)."""
+    import torch
+    r, c, B = 70000, 85000, 5000
+    img = synth.intensity_u16(r, c, synth.DEFAULT_SEED + 5, 50000)
+    h = torch.from_numpy(img.view(np.int16)).pin_memory()
+    wins = [(256, 256, 16, 16), (1024, 1024, 16, 16)]
+    with pytest.raises(swa.SwaError) as ei:
+        swa.analyze(h, wins[:1])
+    assert ei.value.status == swa.SWA_EOVERFLOW
+    res = swa.analyze(h, wins, band_rows=B)
+    for (wh, ww, sy, sx), got in zip(wins, res):
+        R, C = got["sum"].shape
+        edge = [max(0, -(-(b * B - wh + 1) // sy)) for b in range(1, r // B)]
+        ii = np.concatenate([[0, R - 1], edge, [e + 1 for e in edge], RNG.integers(0, R, 40)])
+        ii = np.minimum(ii, R - 1)
+        jj = RNG.integers(0, C, len(ii))
+        for i, j in zip(ii, jj):
+            s, _, m, d = oracle.window_one(img, int(i) * sy, int(j) * sx, wh, ww)
+            assert int(u64(got["sum"][i:i + 1, j:j + 1])[0, 0]) == s, (wh, i, j)
+            assert f64(got["mean"][i:i + 1, j:j + 1])[0, 0] == m
+            assert f64(got["std"][i:i + 1, j:j + 1])[0, 0] == d
+    del h, res

@@ -44,7 +44,13 @@ def test_results_identical_alone_and_in_the_mix():
                + output_bytes(*pool_np[q.image_id].shape, q.windows)
                + pool_np[q.image_id].nbytes for q in reqs)
     tab = [table_bytes(*a.shape, 1 + (k % 2))[0] for k, a in enumerate(pool_np)]
-    server = Server(budget_bytes=need + 2 * max(tab), streams=3, slots=6)
+    # The budget holds the largest request plus half the largest table, well
+    # under the tables of all requested images together, so building them all
+    # must evict.
+    requested = {q.image_id for q in reqs}
+    budget = need + max(tab) // 2
+    assert sum(tab[k] for k in requested) > budget
+    server = Server(budget_bytes=budget, streams=3, slots=6)
     server.run(reqs, realtime=False)
     assert len(server.completed) == 30
     assert server.hits > 0 and server.misses > 0 and server.evictions > 0

@@ -38,3 +38,55 @@ def test_reserve_fails_when_everything_is_referenced():
     assert c.reserve(20) and FakeSat.freed == ["x"] and c.used == 20
     c.release(20)
     assert c.used == 0
+
+
+def test_failed_reserve_evicts_nothing():
+    FakeSat.freed = []
+    c = TableCache(100)
+    for k, refs in (("a", 0), ("b", 1)):
+        assert c.reserve(40)
+        c.insert(k, _Entry(FakeSat(k), 40, refs=refs))
+    # 80 used, only a (40) can go: 80 - 40 + 70 > 100, so nothing is evicted
+    assert not c.reserve(70)
+    assert FakeSat.freed == [] and c.used == 80 and list(c.entries) == ["a", "b"]
+    assert c.reserve(50) and FakeSat.freed == ["a"] and c.used == 90
+
+
+def _fake_server(fits, slots=8, lookahead=8, max_bypass=16):
+    """A Server whose admission test is `fits(request)`; no device needed."""
+    import collections
+    from paper_2410_16291_gb300.serve import Request, Server
+    sv = object.__new__(Server)
+    sv.slots, sv.lookahead, sv.max_bypass = slots, lookahead, max_bypass
+    sv.inflight, sv.waiting = [], collections.deque()
+    order = []
+
+    def try_admit(req, now):
+        if not fits(req):
+            return False
+        order.append(req.rid)
+        sv.inflight.append(req)
+        return True
+    sv._try_admit = try_admit
+    return sv, order, Request
+
+
+def test_admission_lets_fitting_requests_pass_a_blocked_head():
+    sv, order, Request = _fake_server(lambda r: r.rid != 0)
+    sv.waiting.extend(Request(i, i, None, []) for i in range(4))
+    assert sv._admit(0.0)
+    assert order == [1, 2, 3] and sv.waiting[0].rid == 0 and sv.waiting[0].bypassed == 3
+
+
+def test_admission_bypass_is_bounded():
+    sv, order, Request = _fake_server(lambda r: r.rid != 0, max_bypass=2)
+    sv.waiting.extend(Request(i, i, None, []) for i in range(5))
+    sv._admit(0.0)
+    assert order == [1, 2] and [r.rid for r in sv.waiting] == [0, 3, 4]
+
+
+def test_admission_respects_slots_and_order():
+    sv, order, Request = _fake_server(lambda r: True, slots=3)
+    sv.waiting.extend(Request(i, i, None, []) for i in range(5))
+    sv._admit(0.0)
+    assert order == [0, 1, 2] and [r.rid for r in sv.waiting] == [3, 4]
