@@ -291,8 +291,8 @@ k_scan(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
     __syncwarp();
 }
 
-template <typename T, bool WQ, bool VEC, int TH>
-__global__ void __launch_bounds__(kOpWarps * 32, 1)
+template <typename T, bool WQ, bool VEC, int TH, int W>
+__global__ void __launch_bounds__(W * 32, 1)
 k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
           const __grid_constant__ CUtensorMap tmQ)
 {
@@ -399,11 +399,23 @@ swa_status dispatch_twopass(const BuildPlan &p, const char *img, uint64_t *S, ui
 
 template <typename T> constexpr int onepass_rows() { return sizeof(T) == 1 ? 64 : 32; }
 
+// Warps per block of the single-pass build: as many independent warps as
+// the shared memory of one SM holds (227 KB per block, 1 KB for alignment),
+// at most 16.  One block runs per SM.
+constexpr int kSmemPerBlock = 227 * 1024;
+template <typename T> constexpr int onepass_warps()
+{
+    return (kSmemPerBlock - 1024) / onepass_warp_bytes<T, onepass_rows<T>()>() < 16
+               ? (kSmemPerBlock - 1024) / onepass_warp_bytes<T, onepass_rows<T>()>()
+               : 16;
+}
+
 template <typename T, bool WQ, bool VEC>
 swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
                           char *scratch, uint32_t *err, cudaStream_t st)
 {
     constexpr int TH = onepass_rows<T>();
+    constexpr int W = onepass_warps<T>();
     OnePass a;
     a.img = img;
     a.pitch = p.pitch;
@@ -428,27 +440,26 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
                   (long long)p.ld);
         return SWA_ECUDA;
     }
-    const size_t smem =
-        1024 + (size_t)kOpWarps * (kRing * 2 * kRowBytes + TH * kSliceCols * sizeof(T));
-    auto kern = k_onepass<T, WQ, VEC, TH>;
+    const size_t smem = 1024 + (size_t)W * onepass_warp_bytes<T, TH>();
+    auto kern = k_onepass<T, WQ, VEC, TH, W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return launch_error("cudaFuncSetAttribute", e);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOpWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
     if (per_sm < 1) per_sm = 1;
     const int64_t tiles = p.nby * p.nsx;
     int64_t blocks = (int64_t)sms * per_sm;
-    const int64_t need = (tiles + kOpWarps - 1) / kOpWarps;
+    const int64_t need = (tiles + W - 1) / W;
     if (blocks > need) blocks = need;
     if ((e = cudaMemsetAsync(scratch + p.off_ticket, 0, p.off_cs - p.off_ticket, st)) !=
         cudaSuccess)
         return launch_error("cudaMemsetAsync", e);
     {
         LaunchScope ls("sat_build", st);
-        kern<<<(unsigned)blocks, kOpWarps * 32, smem, st>>>(a, tmS, tmQ);
+        kern<<<(unsigned)blocks, W * 32, smem, st>>>(a, tmS, tmQ);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return launch_error("SAT build launch failed", e);

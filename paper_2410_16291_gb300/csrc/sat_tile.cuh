@@ -228,7 +228,6 @@ __device__ __forceinline__ void emit_row(unsigned char *ring, int &slot, const i
 // expiry the warp sets the error word and all warps stop.
 constexpr uint32_t kAgg = 1u, kInc = 2u;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
-constexpr int kOpWarps = 8;                        // warps per block (independent tiles)
 
 struct OnePass {
     const char *img;
@@ -369,26 +368,32 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     {
         uint32_t c32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        // Rows go in groups of 32 (group j unrolled, so rs_s[j] and rs_q[j]
+        // have compile-time indices and stay in registers).
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) { rs_s[j] = 0; rs_q[j] = 0; }
-        for (int r = 0; r < nr; ++r) {
-            uint32_t px[8];
-            smem8<T>(tile + r * kSliceCols, lane, px);
-            uint32_t rs = 0;
-            QA rq = 0;
+        for (int j = 0; j < RPL; ++j) {
+            rs_s[j] = 0;
+            rs_q[j] = 0;
+            const int rend = min(nr, 32 * (j + 1));
+            for (int r = 32 * j; r < rend; ++r) {
+                uint32_t px[8];
+                smem8<T>(tile + r * kSliceCols, lane, px);
+                uint32_t rs = 0;
+                QA rq = 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                c32[k] += px[k];
-                rs += px[k];
-                if (WQ) {
-                    const QA p2 = (QA)px[k] * (QA)px[k];
-                    cqa[k] += p2;
-                    rq += p2;
+                for (int k = 0; k < 8; ++k) {
+                    c32[k] += px[k];
+                    rs += px[k];
+                    if (WQ) {
+                        const QA p2 = (QA)px[k] * (QA)px[k];
+                        cqa[k] += p2;
+                        rq += p2;
+                    }
                 }
+                const uint64_t row_s = warp_sum(rs);
+                const uint64_t row_q = WQ ? (uint64_t)warp_sum(rq) : 0;
+                if ((r & 31) == lane) { rs_s[j] = row_s; rs_q[j] = row_q; }
             }
-            const uint64_t row_s = warp_sum(rs);
-            const uint64_t row_q = WQ ? (uint64_t)warp_sum(rq) : 0;
-            if ((r & 31) == lane) { rs_s[r >> 5] = row_s; rs_q[r >> 5] = row_q; }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) { cs[k] = c32[k]; cq[k] = cqa[k]; }
@@ -494,55 +499,57 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint64_t H_s = 0, H_q = 0;
     const int c1 = (int)(s * (kSliceCols / 16));
-    for (int r = 0; r < nr; r += 2) {
-        uint32_t pa[8], pb[8];
-        smem8<T>(tile + r * kSliceCols, lane, pa);
-        smem8<T>(tile + (r + 1) * kSliceCols, lane, pb);   // row r+1 < TH exists in the buffer
-        uint64_t ls = lr_s[0], lq = lr_q[0];
 #pragma unroll
-        for (int j = 1; j < RPL; ++j)
-            if ((r >> 5) == j) { ls = lr_s[j]; lq = lr_q[j]; }
-        // r is even, so rows r and r+1 lie in the same group of 32.
-        const uint64_t ha_s = H_s + __shfl_sync(kFull, ls, r & 31);
-        const uint64_t hb_s = ha_s + __shfl_sync(kFull, ls, (r + 1) & 31);
-        uint64_t ha_q = 0, hb_q = 0;
-        if (WQ) {
-            ha_q = H_q + __shfl_sync(kFull, lq, r & 31);
-            hb_q = ha_q + __shfl_sync(kFull, lq, (r + 1) & 31);
-        }
-        H_s = hb_s;
-        H_q = hb_q;
-        uint32_t la[8], lb[8];
-        QA qa[8], qb[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            cp[k] += pa[k];
-            la[k] = cp[k] + (k ? la[k - 1] : 0u);
-            cp[k] += pb[k];
-            lb[k] = cp[k] + (k ? lb[k - 1] : 0u);
+    for (int j = 0; j < RPL; ++j) {
+        // Group j of 32 rows (unrolled: lr_s[j] has a compile-time index).
+        const uint64_t ls = lr_s[j], lq = lr_q[j];
+        const int rend = min(nr, 32 * (j + 1));
+        for (int r = 32 * j; r < rend; r += 2) {
+            uint32_t pa[8], pb[8];
+            smem8<T>(tile + r * kSliceCols, lane, pa);
+            smem8<T>(tile + (r + 1) * kSliceCols, lane, pb);   // row r+1 < TH exists in the buffer
+            // r is even, so rows r and r+1 lie in the same group of 32.
+            const uint64_t ha_s = H_s + __shfl_sync(kFull, ls, r & 31);
+            const uint64_t hb_s = ha_s + __shfl_sync(kFull, ls, (r + 1) & 31);
+            uint64_t ha_q = 0, hb_q = 0;
             if (WQ) {
-                cqa[k] += (QA)pa[k] * (QA)pa[k];
-                qa[k] = cqa[k] + (k ? qa[k - 1] : (QA)0);
-                cqa[k] += (QA)pb[k] * (QA)pb[k];
-                qb[k] = cqa[k] + (k ? qb[k - 1] : (QA)0);
+                ha_q = H_q + __shfl_sync(kFull, lq, r & 31);
+                hb_q = ha_q + __shfl_sync(kFull, lq, (r + 1) & 31);
             }
+            H_s = hb_s;
+            H_q = hb_q;
+            uint32_t la[8], lb[8];
+            QA qa[8], qb[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                cp[k] += pa[k];
+                la[k] = cp[k] + (k ? la[k - 1] : 0u);
+                cp[k] += pb[k];
+                lb[k] = cp[k] + (k ? lb[k - 1] : 0u);
+                if (WQ) {
+                    cqa[k] += (QA)pa[k] * (QA)pa[k];
+                    qa[k] = cqa[k] + (k ? qa[k - 1] : (QA)0);
+                    cqa[k] += (QA)pb[k] * (QA)pb[k];
+                    qb[k] = cqa[k] + (k ? qb[k - 1] : (QA)0);
+                }
+            }
+            const uint32_t isa = warp_incl_scan(la[7], lane);
+            const uint32_t isb = warp_incl_scan(lb[7], lane);
+            const uint64_t base_as = ha_s + (uint64_t)(isa - la[7]);
+            const uint64_t base_bs = hb_s + (uint64_t)(isb - lb[7]);
+            uint64_t base_aq = 0, base_bq = 0;
+            if (WQ) {
+                const QA iqa = warp_incl_scan(qa[7], lane);
+                const QA iqb = warp_incl_scan(qb[7], lane);
+                base_aq = ha_q + (uint64_t)(iqa - qa[7]);
+                base_bq = hb_q + (uint64_t)(iqb - qb[7]);
+            }
+            emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_as, vs, la, base_aq, vq, qa, a.tmS,
+                             a.tmQ, c1, (int)(y0 + r), w.pol);
+            if (r + 1 < nr)
+                emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_bs, vs, lb, base_bq, vq, qb, a.tmS, a.tmQ,
+                                 c1, (int)(y0 + r + 1), w.pol);
         }
-        const uint32_t isa = warp_incl_scan(la[7], lane);
-        const uint32_t isb = warp_incl_scan(lb[7], lane);
-        const uint64_t base_as = ha_s + (uint64_t)(isa - la[7]);
-        const uint64_t base_bs = hb_s + (uint64_t)(isb - lb[7]);
-        uint64_t base_aq = 0, base_bq = 0;
-        if (WQ) {
-            const QA iqa = warp_incl_scan(qa[7], lane);
-            const QA iqb = warp_incl_scan(qb[7], lane);
-            base_aq = ha_q + (uint64_t)(iqa - qa[7]);
-            base_bq = hb_q + (uint64_t)(iqb - qb[7]);
-        }
-        emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_as, vs, la, base_aq, vq, qa, a.tmS, a.tmQ, c1,
-                         (int)(y0 + r), w.pol);
-        if (r + 1 < nr)
-            emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_bs, vs, lb, base_bq, vq, qb, a.tmS, a.tmQ,
-                             c1, (int)(y0 + r + 1), w.pol);
     }
     __syncwarp();     // the tile buffer is reused by the next ticket
     return true;
