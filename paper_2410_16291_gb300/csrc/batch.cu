@@ -31,7 +31,7 @@
 namespace swa {
 namespace {
 
-struct alignas(64) BImg {
+struct alignas(128) BImg {
     CUtensorMap tmS, tmQ;             // TMA views of this image's tables
     const char *img;
     int64_t pitch, rows, cols, nby, nsx, ld;
@@ -60,7 +60,7 @@ struct BatchArgs {
     uint32_t *ticket, *err;
 };
 
-constexpr int kBatchWarps = 8;
+constexpr int kBatchWarps = 9;
 // Shared memory per warp: the larger of the uint8 (64-row) and uint16 tile
 // routines, so warps working on different dtypes never overlap.
 constexpr int kBatchWarpBytes =
@@ -89,9 +89,8 @@ __device__ __forceinline__ int find_base(int n, uint32_t t, F base)
 
 template <typename T, bool VEC, int TH>
 __device__ __forceinline__ bool batch_tile(const BImg &im, uint32_t t, uint32_t *err,
-                                           unsigned char *smem_raw)
+                                           WarpRes &w)
 {
-    WarpRes<T> w = warp_res<T, TH>(smem_raw, kBatchWarpBytes);
     TileCtx c;
     c.img = im.img;
     c.pitch = im.pitch;
@@ -172,27 +171,36 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_batch(const __grid_cons
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
+    // The warp's ring and staging area persist across tiles and images (the
+    // ring's slot order carries over, so no tile waits for the previous
+    // tile's stores to finish).
+    WarpRes w = warp_res<uint8_t, TH8>(smem_raw, kBatchWarpBytes);
+    // A warp's tickets only increase, so it caches the ticket range of its
+    // current image and searches only past it.
+    int k = 0;
+    uint32_t lo = a.imgs[0].tile_base, hi = lo + a.imgs[0].ntiles;
     for (;;) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(a.ticket, 1u);
         t = __shfl_sync(kFull, t, 0);
         if (t >= a.total_tiles || *(volatile uint32_t *)a.err) break;
-        const int k = find_base(a.nimg, t, [&](int i) { return a.imgs[i].tile_base; });
+        if (t < lo || t >= hi) {
+            k += find_base(a.nimg - k, t, [&](int i) { return a.imgs[k + i].tile_base; });
+            lo = a.imgs[k].tile_base;
+            hi = lo + a.imgs[k].ntiles;
+        }
         const BImg &im = a.imgs[k];
-        const uint32_t tl = t - im.tile_base;
+        const uint32_t tl = t - lo;
         tensormap_acquire(&im.tmS);
         tensormap_acquire(&im.tmQ);
         bool ok;
         if (im.dtype == SWA_U8)
-            ok = im.vec ? batch_tile<uint8_t, true, TH8>(im, tl, a.err, smem_raw)
-                        : batch_tile<uint8_t, false, TH8>(im, tl, a.err, smem_raw);
+            ok = im.vec ? batch_tile<uint8_t, true, TH8>(im, tl, a.err, w)
+                        : batch_tile<uint8_t, false, TH8>(im, tl, a.err, w);
         else
-            ok = im.vec ? batch_tile<uint16_t, true, 32>(im, tl, a.err, smem_raw)
-                        : batch_tile<uint16_t, false, 32>(im, tl, a.err, smem_raw);
+            ok = im.vec ? batch_tile<uint16_t, true, 32>(im, tl, a.err, w)
+                        : batch_tile<uint16_t, false, 32>(im, tl, a.err, w);
         if (!ok) break;
-        // the next ticket reuses the ring from slot 0
-        if (lane == 0) bulk_wait_all();
-        __syncwarp();
     }
     cp_async_wait_all();
     if (lane == 0) bulk_wait_all();

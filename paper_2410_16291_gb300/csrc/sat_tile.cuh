@@ -46,13 +46,35 @@ __device__ __forceinline__ Raw8<T> load_raw8(const char *__restrict__ img, int64
             r.w[3 % (sizeof(T) * 2)] = v.w;
         }
     } else {
+        // Any (even, for uint16) byte alignment: the 8-byte-aligned words that
+        // cover the chunk, shifted by its misalignment, when they lie inside
+        // the row; byte by byte near the row's ends.
+        const char *rowc = img + y * pitch;
+        const int64_t rowbytes = cols * (int64_t)sizeof(T);
+        const int64_t cb = x * (int64_t)sizeof(T);
+        const int m = (int)(reinterpret_cast<uintptr_t>(rowc + cb) & 7u);
+        constexpr int NW = sizeof(T) == 1 ? 2 : 3;
+        if (cb - m >= 0 && cb - m + 8 * NW <= rowbytes) {
+            const unsigned long long *wp =
+                reinterpret_cast<const unsigned long long *>(rowc + cb - m);
+            uint64_t wv[NW];
 #pragma unroll
-        for (int i = 0; i < (int)sizeof(T) * 2; ++i) r.w[i] = 0;
+            for (int i = 0; i < NW; ++i) wv[i] = __ldg(wp + i);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t v = (x + k < cols) ? (uint32_t)__ldg(row + x + k) : 0u;
-            if (sizeof(T) == 1) r.w[k >> 2] |= v << (8 * (k & 3));
-            else r.w[(k >> 1) % (sizeof(T) * 2)] |= v << (16 * (k & 1));
+            for (int i = 0; i < NW - 1; ++i) {
+                const uint64_t v = m ? (wv[i] >> (8 * m)) | (wv[i + 1] << (64 - 8 * m)) : wv[i];
+                r.w[(2 * i) % (sizeof(T) * 2)] = (uint32_t)v;
+                r.w[(2 * i + 1) % (sizeof(T) * 2)] = (uint32_t)(v >> 32);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < (int)sizeof(T) * 2; ++i) r.w[i] = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t v = (x + k < cols) ? (uint32_t)__ldg(row + x + k) : 0u;
+                if (sizeof(T) == 1) r.w[k >> 2] |= v << (8 * (k & 3));
+                else r.w[(k >> 1) % (sizeof(T) * 2)] |= v << (16 * (k & 1));
+            }
         }
     }
     return r;
@@ -104,6 +126,39 @@ __device__ __forceinline__ void smem8(const T *row, int lane, uint32_t px[8])
         px[2] = v.y & 0xffffu; px[3] = v.y >> 16;
         px[4] = v.z & 0xffffu; px[5] = v.z >> 16;
         px[6] = v.w & 0xffffu; px[7] = v.w >> 16;
+    }
+}
+
+// Bytes per staged tile row: the slice's pixels plus one 8-byte word, so an
+// unaligned row can be staged as the aligned words covering it; uint16 rows
+// are padded to a multiple of 16 bytes so aligned rows keep 16-byte copies.
+template <typename T>
+constexpr int tile_row_bytes() { return sizeof(T) == 1 ? 256 + 8 : 512 + 16; }
+
+// The lane's 8 pixels of one staged row.  VEC rows hold the slice's pixels
+// from byte 0; other rows hold the aligned words covering the slice, whose
+// pixels start m bytes in (m = the row's misalignment, 0..7).
+template <typename T, bool VEC>
+__device__ __forceinline__ void staged8(const unsigned char *row, int lane, int m, uint32_t px[8])
+{
+    if (VEC) {
+        smem8<T>(reinterpret_cast<const T *>(row), lane, px);
+    } else if (sizeof(T) == 1) {
+        const uint64_t *w = reinterpret_cast<const uint64_t *>(row) + lane;
+        const uint64_t lo = w[0], hi = w[1];
+        const uint64_t v = m ? (lo >> (8 * m)) | (hi << (64 - 8 * m)) : lo;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) px[k] = (uint32_t)(v >> (8 * k)) & 0xffu;
+    } else {
+        const uint64_t *w = reinterpret_cast<const uint64_t *>(row) + 2 * lane;
+        const uint64_t w0 = w[0], w1 = w[1], w2 = w[2];
+        const uint64_t v0 = m ? (w0 >> (8 * m)) | (w1 << (64 - 8 * m)) : w0;
+        const uint64_t v1 = m ? (w1 >> (8 * m)) | (w2 << (64 - 8 * m)) : w1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            px[k] = (uint32_t)(v0 >> (16 * k)) & 0xffffu;
+            px[k + 4] = (uint32_t)(v1 >> (16 * k)) & 0xffffu;
+        }
     }
 }
 
@@ -281,11 +336,12 @@ __device__ __noinline__ uint32_t wait_flag(const uint32_t *flag, uint32_t *err)
 }
 
 // Every lane has written its part of the records; make them visible, then
-// raise up to two flags (a fence followed by relaxed stores is a release).
+// raise up to two flags (an acquire-release fence followed by relaxed stores
+// is a release; the readers' ld.acquire pairs with it).
 __device__ __forceinline__ void publish(uint32_t *f1, uint32_t v1, uint32_t *f2 = nullptr,
                                         uint32_t v2 = 0)
 {
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
         st_relaxed(f1, v1);
@@ -320,10 +376,10 @@ struct TileCtx {
     const CUtensorMap *tmS, *tmQ;
 };
 
-// Per-warp resources of the tile routine.
-template <typename T>
+// Per-warp resources of the tile routine (the same for every pixel type, so
+// one warp can move between images of different types and keep its ring).
 struct WarpRes {
-    T *tile;                          // TH x 256 staged pixels
+    unsigned char *tile;              // staged rows of tile_row_bytes<T>()
     unsigned char *ring;              // [kRing][S, Q][2 KB]
     int slot;
     int sw[4];
@@ -335,28 +391,62 @@ struct WarpRes {
 // word is then set).
 template <typename T, bool WQ, bool VEC, int TH>
 __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint32_t *err,
-                                             WarpRes<T> &w)
+                                             WarpRes &w)
 {
     using QA = typename QAcc<T>::type;
     constexpr int RPL = TH / 32;                       // rows each lane keeps
     constexpr int HREC = 2 * TH + 2;                   // horizontal record length
     const int lane = threadIdx.x & 31;
-    T *tile = w.tile;
+    constexpr int RB = tile_row_bytes<T>();
+    unsigned char *tile = w.tile;
     const int64_t b = t / a.nsx, s = t % a.nsx;
     const int64_t y0 = b * TH;
     const int nr = (int)min((int64_t)TH, a.rows - y0);
     const int64_t x = s * kSliceCols + lane * kPxPerLane;
+    const int64_t rowbytes = a.cols * (int64_t)sizeof(T);
+    const int64_t xb = s * kSliceCols * (int64_t)sizeof(T);     // slice start in a row
+    // Misalignment of the slice's first pixel in row r of the tile (0 with VEC).
+    auto mis = [&](int r) -> int {
+        return VEC ? 0
+                   : (int)(reinterpret_cast<uintptr_t>(a.img + (y0 + r) * a.pitch + xb) & 7u);
+    };
 
-    // Stage the tile (rows 0..nr-1; columns past the image read as 0).
+    // Stage the tile (rows 0..nr-1; columns past the image read as 0).  With
+    // VEC every lane copies its 8 pixels with one cp.async.  Otherwise a row
+    // may start at any (even, for uint16) byte address: the warp copies the
+    // 8-byte-aligned words covering the slice (lane l words l*sizeof(T) +
+    // i, lane 31 one more), and staged8 shifts by the row's misalignment.
+    // Words that straddle an end of the row go byte by byte, zero outside it.
     for (int r = 0; r < nr; ++r) {
-        T *dst = tile + r * kSliceCols + lane * 8;
-        const T *src = reinterpret_cast<const T *>(a.img + (y0 + r) * a.pitch) + x;
-        if (VEC && x + 8 <= a.cols) {
-            if (sizeof(T) == 1) cp_async8(dst, src);
-            else cp_async16(dst, src);
-        } else {
+        unsigned char *drow = tile + r * RB;
+        const char *row = a.img + (y0 + r) * a.pitch;
+        if (VEC) {
+            T *dst = reinterpret_cast<T *>(drow) + lane * 8;
+            const T *src = reinterpret_cast<const T *>(row) + x;
+            if (x + 8 <= a.cols) {
+                if (sizeof(T) == 1) cp_async8(dst, src);
+                else cp_async16(dst, src);
+            } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) dst[k] = (x + k < a.cols) ? src[k] : (T)0;
+                for (int k = 0; k < 8; ++k) dst[k] = (x + k < a.cols) ? src[k] : (T)0;
+            }
+        } else {
+            const int m = mis(r);
+            const int nw = (int)sizeof(T) + (lane == 31 ? 1 : 0);
+            for (int i = 0; i < nw; ++i) {
+                const int k = lane * (int)sizeof(T) + i;
+                const int64_t off = xb - m + 8 * k;           // word's offset in the row
+                unsigned char *d = drow + 8 * k;
+                if (off >= 0 && off + 8 <= rowbytes) {
+                    cp_async8(d, row + off);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int64_t o = off + j;
+                        d[j] = (o >= 0 && o < rowbytes) ? (unsigned char)row[o] : 0u;
+                    }
+                }
+            }
         }
     }
     cp_async_wait_all();
@@ -377,7 +467,7 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
             const int rend = min(nr, 32 * (j + 1));
             for (int r = 32 * j; r < rend; ++r) {
                 uint32_t px[8];
-                smem8<T>(tile + r * kSliceCols, lane, px);
+                staged8<T, VEC>(tile + r * RB, lane, mis(r), px);
                 uint32_t rs = 0;
                 QA rq = 0;
 #pragma unroll
@@ -506,8 +596,9 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
         const int rend = min(nr, 32 * (j + 1));
         for (int r = 32 * j; r < rend; r += 2) {
             uint32_t pa[8], pb[8];
-            smem8<T>(tile + r * kSliceCols, lane, pa);
-            smem8<T>(tile + (r + 1) * kSliceCols, lane, pb);   // row r+1 < TH exists in the buffer
+            staged8<T, VEC>(tile + r * RB, lane, mis(r), pa);
+            // Row r+1 < TH exists in the buffer (stale when r+1 == nr, unused).
+            staged8<T, VEC>(tile + (r + 1) * RB, lane, mis(r + 1), pb);
             // r is even, so rows r and r+1 lie in the same group of 32.
             const uint64_t ha_s = H_s + __shfl_sync(kFull, ls, r & 31);
             const uint64_t hb_s = ha_s + __shfl_sync(kFull, ls, (r + 1) & 31);
@@ -559,21 +650,21 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
 template <typename T, int TH>
 constexpr int onepass_warp_bytes()
 {
-    return kRing * 2 * kRowBytes + TH * kSliceCols * (int)sizeof(T);
+    return (kRing * 2 * kRowBytes + TH * tile_row_bytes<T>() + 1023) / 1024 * 1024;
 }
 
 // The warp's ring and tile inside the block's dynamic shared memory; warps
 // are `stride` bytes apart (a multiple of 1024, at least the routine's need).
 template <typename T, int TH>
-__device__ __forceinline__ WarpRes<T> warp_res(unsigned char *smem_raw,
-                                               int stride = onepass_warp_bytes<T, TH>())
+__device__ __forceinline__ WarpRes warp_res(unsigned char *smem_raw,
+                                            int stride = onepass_warp_bytes<T, TH>())
 {
     static_assert(onepass_warp_bytes<T, TH>() % 1024 == 0, "ring slots stay 1024-byte aligned");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned char *base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-    WarpRes<T> w;
+    WarpRes w;
     w.ring = base + (size_t)warp * stride;
-    w.tile = reinterpret_cast<T *>(w.ring + kRing * 2 * kRowBytes);
+    w.tile = w.ring + kRing * 2 * kRowBytes;
     w.slot = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) w.sw[j] = swz_off(lane, j);
