@@ -33,6 +33,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SAT build Gpx/s + window outputs/s, % HBM peak; served p50/p99 vs plain path"
+# Thread instructions per window (sum, mean, std; 4 windows per thread) of
+# the window kernel, from ncu on the 12,288^2 stride-1 case
+# (profiles/window_stats_12288x12288.md).
+INSTR_PER_WINDOW = 475.0
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -381,9 +385,26 @@ def run_ours(args, rank, world, local_rank):
                         "sat_reduce": px * 1}
     win_bytes = sum(distinct_corner_bytes(im.rows, im.cols, *w, tables) + 24 * R * C
                     for w, (R, C) in zip(windows, shapes))
-    bytes_per_launch["window_stats"] = win_bytes / len(windows)
+    win_launches = kernels.get("window_stats", {}).get("launches", 0)
+    bytes_per_launch["window_stats"] = win_bytes * args.steps / max(1, win_launches)
     roof = None
-    if dom is not None and dom in bytes_per_launch:
+    if dom == "window_stats" and all(w[3] < 4 for w in windows):
+        # Dense column strides: the exact mean/std arithmetic bounds the
+        # kernel by instruction issue.  Peak = SMs x 4 schedulers x 32 lanes x
+        # the SM clock sampled during the run; achieved = windows/s x the
+        # instructions per window ncu measured for this kernel (sum, mean and
+        # std at stride 1, profiles/window_stats_12288x12288.md).
+        n_win = sum(R * C for R, C in shapes)
+        sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak_t = sms * 4 * 32 * mhz * 1e6 / 1e12
+        ach_t = n_win / (kernels[dom]["avg_ms"] * win_launches / args.steps / 1e3) * \
+            INSTR_PER_WINDOW / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach_t, "peak": peak_t,
+                "unit": "Tinst/s", "frac": ach_t / peak_t, "peak_kind": "issue rate at the "
+                "sampled SM clock", "instructions_per_window": INSTR_PER_WINDOW,
+                "traffic": None, "avg_ms": kernels[dom]["avg_ms"]}
+    elif dom is not None and dom in bytes_per_launch:
         avg = kernels[dom]["avg_ms"]
         ach = bytes_per_launch[dom] / (avg / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",

@@ -24,6 +24,8 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <mutex>
 
@@ -291,14 +293,15 @@ k_scan(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
     __syncwarp();
 }
 
-template <typename T, bool WQ, bool VEC, int TH, int W>
+template <typename T, bool WQ, bool VEC, int TH, int W, bool DIRECT>
 __global__ void __launch_bounds__(W * 32, 1)
 k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
           const __grid_constant__ CUtensorMap tmQ)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
-    WarpRes<T> w = warp_res<T, TH>(smem_raw);
+    WarpRes w = DIRECT ? warp_res<T, TH>(smem_raw, direct_warp_bytes())
+                       : warp_res<T, TH>(smem_raw);
     TileCtx c;
     c.img = a.img;
     c.pitch = a.pitch;
@@ -321,7 +324,9 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
         t = __shfl_sync(kFull, t, 0);
         if ((int64_t)t >= ntiles || *(volatile uint32_t *)a.err) break;
         if (t == 0 && a.stall_tile0) continue;
-        if (!onepass_tile<T, WQ, VEC, TH>(c, t, a.err, w)) break;
+        const bool ok = DIRECT ? onepass_tile_direct<T, WQ, VEC, TH>(c, t, a.err, w)
+                               : onepass_tile<T, WQ, VEC, TH>(c, t, a.err, w);
+        if (!ok) break;
     }
     cp_async_wait_all();
     if (lane == 0) bulk_wait_all();
@@ -398,6 +403,9 @@ swa_status dispatch_twopass(const BuildPlan &p, const char *img, uint64_t *S, ui
 }
 
 template <typename T> constexpr int onepass_rows() { return sizeof(T) == 1 ? 64 : 32; }
+// Rows per tile of the direct variant (no staging, so taller tiles fit).
+template <typename T> constexpr int direct_rows() { return sizeof(T) == 1 ? 128 : 64; }
+constexpr int kDirectWarps = 16;
 
 // Warps per block of the single-pass build: as many independent warps as
 // the shared memory of one SM holds (227 KB per block, 1 KB for alignment),
@@ -410,12 +418,12 @@ template <typename T> constexpr int onepass_warps()
                : 16;
 }
 
-template <typename T, bool WQ, bool VEC>
+template <typename T, bool WQ, bool VEC, bool DIRECT>
 swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
                           char *scratch, uint32_t *err, cudaStream_t st)
 {
-    constexpr int TH = onepass_rows<T>();
-    constexpr int W = onepass_warps<T>();
+    constexpr int TH = DIRECT ? direct_rows<T>() : onepass_rows<T>();
+    constexpr int W = DIRECT ? kDirectWarps : onepass_warps<T>();
     OnePass a;
     a.img = img;
     a.pitch = p.pitch;
@@ -440,8 +448,9 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
                   (long long)p.ld);
         return SWA_ECUDA;
     }
-    const size_t smem = 1024 + (size_t)W * onepass_warp_bytes<T, TH>();
-    auto kern = k_onepass<T, WQ, VEC, TH, W>;
+    const size_t smem =
+        1024 + (size_t)W * (DIRECT ? direct_warp_bytes() : onepass_warp_bytes<T, TH>());
+    auto kern = k_onepass<T, WQ, VEC, TH, W, DIRECT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return launch_error("cudaFuncSetAttribute", e);
@@ -470,11 +479,18 @@ template <typename T>
 swa_status dispatch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
                             char *scratch, uint32_t *err, cudaStream_t st)
 {
+    if (p.direct) {
+        if (p.with_q)
+            return p.vec ? launch_onepass<T, true, true, true>(p, img, S, Q, scratch, err, st)
+                         : launch_onepass<T, true, false, true>(p, img, S, Q, scratch, err, st);
+        return p.vec ? launch_onepass<T, false, true, true>(p, img, S, Q, scratch, err, st)
+                     : launch_onepass<T, false, false, true>(p, img, S, Q, scratch, err, st);
+    }
     if (p.with_q)
-        return p.vec ? launch_onepass<T, true, true>(p, img, S, Q, scratch, err, st)
-                     : launch_onepass<T, true, false>(p, img, S, Q, scratch, err, st);
-    return p.vec ? launch_onepass<T, false, true>(p, img, S, Q, scratch, err, st)
-                 : launch_onepass<T, false, false>(p, img, S, Q, scratch, err, st);
+        return p.vec ? launch_onepass<T, true, true, false>(p, img, S, Q, scratch, err, st)
+                     : launch_onepass<T, true, false, false>(p, img, S, Q, scratch, err, st);
+    return p.vec ? launch_onepass<T, false, true, false>(p, img, S, Q, scratch, err, st)
+                 : launch_onepass<T, false, false, false>(p, img, S, Q, scratch, err, st);
 }
 
 int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
@@ -496,8 +512,13 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
     // address and the pitch aligned to the vector size.
     const int64_t vbytes = dtype == SWA_U8 ? 8 : 16;
     p.vec = ((uintptr_t)image % vbytes == 0) && (pitch % vbytes == 0);
-    p.th = p.twopass ? kTH : (dtype == SWA_U8 ? onepass_rows<uint8_t>()
-                                              : onepass_rows<uint16_t>());
+    // Single-pass variant: staged tiles by default; SWA_SAT_VARIANT=direct
+    // selects the variant that reads each tile twice instead (an ablation).
+    const char *var = getenv("SWA_SAT_VARIANT");
+    p.direct = !p.twopass && var && strcmp(var, "direct") == 0;
+    p.th = p.twopass  ? kTH
+           : p.direct ? (dtype == SWA_U8 ? direct_rows<uint8_t>() : direct_rows<uint16_t>())
+                      : (dtype == SWA_U8 ? onepass_rows<uint8_t>() : onepass_rows<uint16_t>());
     p.nby = (rows + p.th - 1) / p.th;
     p.nsx = (cols + kSliceCols - 1) / kSliceCols;
     int64_t off = 0;

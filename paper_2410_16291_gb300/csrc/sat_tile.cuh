@@ -129,31 +129,34 @@ __device__ __forceinline__ void smem8(const T *row, int lane, uint32_t px[8])
     }
 }
 
-// Bytes per staged tile row: the slice's pixels plus one 8-byte word, so an
-// unaligned row can be staged as the aligned words covering it; uint16 rows
-// are padded to a multiple of 16 bytes so aligned rows keep 16-byte copies.
+// Bytes per staged tile row: the slice's pixels plus one 16-byte chunk, so
+// an unaligned row can be staged as the 16-byte-aligned chunks covering it.
 template <typename T>
-constexpr int tile_row_bytes() { return sizeof(T) == 1 ? 256 + 8 : 512 + 16; }
+constexpr int tile_row_bytes() { return kSliceCols * (int)sizeof(T) + 16; }
 
 // The lane's 8 pixels of one staged row.  VEC rows hold the slice's pixels
-// from byte 0; other rows hold the aligned words covering the slice, whose
-// pixels start m bytes in (m = the row's misalignment, 0..7).
+// from byte 0; other rows hold the 16-byte-aligned chunks covering the
+// slice, whose pixels start m bytes in (m = the row's misalignment, 0..15).
 template <typename T, bool VEC>
 __device__ __forceinline__ void staged8(const unsigned char *row, int lane, int m, uint32_t px[8])
 {
     if (VEC) {
         smem8<T>(reinterpret_cast<const T *>(row), lane, px);
-    } else if (sizeof(T) == 1) {
-        const uint64_t *w = reinterpret_cast<const uint64_t *>(row) + lane;
+        return;
+    }
+    // The lane's bytes start at m + 8*sizeof(T)*lane: word j = that / 8,
+    // shifted right by sh bits across the following word(s).
+    const uint64_t *w = reinterpret_cast<const uint64_t *>(row) + (m >> 3) + lane * sizeof(T);
+    const int sh = (m & 7) * 8;
+    if (sizeof(T) == 1) {
         const uint64_t lo = w[0], hi = w[1];
-        const uint64_t v = m ? (lo >> (8 * m)) | (hi << (64 - 8 * m)) : lo;
+        const uint64_t v = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
 #pragma unroll
         for (int k = 0; k < 8; ++k) px[k] = (uint32_t)(v >> (8 * k)) & 0xffu;
     } else {
-        const uint64_t *w = reinterpret_cast<const uint64_t *>(row) + 2 * lane;
         const uint64_t w0 = w[0], w1 = w[1], w2 = w[2];
-        const uint64_t v0 = m ? (w0 >> (8 * m)) | (w1 << (64 - 8 * m)) : w0;
-        const uint64_t v1 = m ? (w1 >> (8 * m)) | (w2 << (64 - 8 * m)) : w1;
+        const uint64_t v0 = sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;
+        const uint64_t v1 = sh ? (w1 >> sh) | (w2 << (64 - sh)) : w1;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             px[k] = (uint32_t)(v0 >> (16 * k)) & 0xffffu;
@@ -386,6 +389,123 @@ struct WarpRes {
     uint64_t pol;
 };
 
+// The look-back of tile t = (b, s) after its reduction (column sums cs/cq,
+// row sums rs_s/rs_q with lane l holding rows l + 32 j): publish the
+// vertical aggregate, look back up the slice for the column carries V,
+// publish the inclusive column prefix with the horizontal aggregate (row
+// sums and the total of V: the corner term of the tiles to the right), look
+// back left for the row carries LR and the corner K, publish the inclusive
+// row prefix.  On return vs/vq hold K + V*[x] (V prefix-summed across the
+// slice) and lr_s/lr_q the row carries; false if a wait gave up.
+template <bool WQ, int TH>
+__device__ __forceinline__ bool lookback_tile(const TileCtx &a, uint32_t t, int64_t b, int64_t s,
+                                              const uint64_t cs[8], const uint64_t cq[8],
+                                              const uint64_t rs_s[TH / 32],
+                                              const uint64_t rs_q[TH / 32], uint32_t *err,
+                                              uint64_t vs[8], uint64_t vq[8],
+                                              uint64_t lr_s[TH / 32], uint64_t lr_q[TH / 32])
+{
+    constexpr int RPL = TH / 32;
+    constexpr int HREC = 2 * TH + 2;                   // horizontal record length
+    const int lane = threadIdx.x & 31;
+    // Vertical: publish the column sums, look back up the slice for V.
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { vs[k] = 0; vq[k] = 0; }
+    uint64_t *inv = a.inc_v + (size_t)t * 512 + lane * 8;
+    if (b > 0) {
+        uint64_t *ag = a.agg_v + (size_t)t * 512 + lane * 8;
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            *reinterpret_cast<ulonglong2 *>(ag + k) = make_ulonglong2(cs[k], cs[k + 1]);
+            if (WQ)
+                *reinterpret_cast<ulonglong2 *>(ag + 256 + k) = make_ulonglong2(cq[k], cq[k + 1]);
+        }
+        publish(a.flag_v + t, kAgg);
+        for (int64_t bb = b - 1; bb >= 0; --bb) {
+            const int64_t u = bb * a.nsx + s;
+            const uint32_t f = wait_flag(a.flag_v + u, err);
+            if (!f) return false;
+            const uint64_t *src = (f == kInc ? a.inc_v : a.agg_v) + (size_t)u * 512 + lane * 8;
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                const ulonglong2 v2 = __ldcg(reinterpret_cast<const ulonglong2 *>(src + k));
+                vs[k] += v2.x;
+                vs[k + 1] += v2.y;
+                if (WQ) {
+                    const ulonglong2 z = __ldcg(reinterpret_cast<const ulonglong2 *>(src + 256 + k));
+                    vq[k] += z.x;
+                    vq[k + 1] += z.y;
+                }
+            }
+            if (f == kInc) break;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        *reinterpret_cast<ulonglong2 *>(inv + k) =
+            make_ulonglong2(vs[k] + cs[k], vs[k + 1] + cs[k + 1]);
+        if (WQ)
+            *reinterpret_cast<ulonglong2 *>(inv + 256 + k) =
+                make_ulonglong2(vq[k] + cq[k], vq[k + 1] + cq[k + 1]);
+    }
+
+    // Horizontal record = (row sums, total of V over the slice); published
+    // with the inclusive vertical record (as inclusive when s == 0).
+    uint64_t vt_s = 0, vt_q = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { vt_s += vs[k]; vt_q += vq[k]; }
+    vt_s = warp_sum(vt_s);
+    if (WQ) vt_q = warp_sum(vt_q);
+    uint64_t K_s = 0, K_q = 0;
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) { lr_s[j] = 0; lr_q[j] = 0; }
+    {
+        uint64_t *rec = (s > 0 ? a.agg_h : a.inc_h) + (size_t)t * HREC;
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            rec[lane + 32 * j] = rs_s[j];
+            if (WQ) rec[TH + lane + 32 * j] = rs_q[j];
+        }
+        if (lane == 0) { rec[2 * TH] = vt_s; rec[2 * TH + 1] = vt_q; }
+        publish(a.flag_v + t, kInc, a.flag_h + t, s > 0 ? kAgg : kInc);
+    }
+    if (s > 0) {
+        for (int64_t ss = s - 1; ss >= 0; --ss) {
+            const int64_t u = b * a.nsx + ss;
+            const uint32_t f = wait_flag(a.flag_h + u, err);
+            if (!f) return false;
+            const uint64_t *src = (f == kInc ? a.inc_h : a.agg_h) + (size_t)u * HREC;
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                lr_s[j] += __ldcg(src + lane + 32 * j);
+                if (WQ) lr_q[j] += __ldcg(src + TH + lane + 32 * j);
+            }
+            K_s += __ldcg(src + 2 * TH);
+            if (WQ) K_q += __ldcg(src + 2 * TH + 1);
+            if (f == kInc) break;
+        }
+        uint64_t *in = a.inc_h + (size_t)t * HREC;
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            in[lane + 32 * j] = lr_s[j] + rs_s[j];
+            if (WQ) in[TH + lane + 32 * j] = lr_q[j] + rs_q[j];
+        }
+        if (lane == 0) { in[2 * TH] = K_s + vt_s; in[2 * TH + 1] = K_q + vt_q; }
+        publish(a.flag_h + t, kInc);
+    }
+
+    // For the scan S = K + H[y] + V*[x] + lp: vs/vq become K + V*.
+#pragma unroll
+    for (int k = 1; k < 8; ++k) { vs[k] += vs[k - 1]; if (WQ) vq[k] += vq[k - 1]; }
+    {
+        const uint64_t is = warp_incl_scan(vs[7], lane), es = is - vs[7];
+        const uint64_t iq = WQ ? warp_incl_scan(vq[7], lane) : 0, eq = iq - vq[7];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { vs[k] += es + K_s; if (WQ) vq[k] += eq + K_q; }
+    }
+    return true;
+}
+
 // Process tile t of one image (single pass): stage, reduce, publish, look
 // back, publish, scan, write.  Returns false if a wait gave up (the error
 // word is then set).
@@ -395,7 +515,6 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
 {
     using QA = typename QAcc<T>::type;
     constexpr int RPL = TH / 32;                       // rows each lane keeps
-    constexpr int HREC = 2 * TH + 2;                   // horizontal record length
     const int lane = threadIdx.x & 31;
     constexpr int RB = tile_row_bytes<T>();
     unsigned char *tile = w.tile;
@@ -405,18 +524,21 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     const int64_t x = s * kSliceCols + lane * kPxPerLane;
     const int64_t rowbytes = a.cols * (int64_t)sizeof(T);
     const int64_t xb = s * kSliceCols * (int64_t)sizeof(T);     // slice start in a row
-    // Misalignment of the slice's first pixel in row r of the tile (0 with VEC).
-    auto mis = [&](int r) -> int {
-        return VEC ? 0
-                   : (int)(reinterpret_cast<uintptr_t>(a.img + (y0 + r) * a.pitch + xb) & 7u);
-    };
+    // Misalignment (mod 16) of the slice's first pixel in row r of the tile;
+    // 0 with VEC.  32-bit arithmetic: only the low four bits matter.
+    const uint32_t m0 = (uint32_t)reinterpret_cast<uintptr_t>(a.img + y0 * a.pitch + xb);
+    const uint32_t pm = (uint32_t)a.pitch;
+    auto mis = [&](int r) -> int { return VEC ? 0 : (int)((m0 + (uint32_t)r * pm) & 15u); };
 
     // Stage the tile (rows 0..nr-1; columns past the image read as 0).  With
     // VEC every lane copies its 8 pixels with one cp.async.  Otherwise a row
     // may start at any (even, for uint16) byte address: the warp copies the
-    // 8-byte-aligned words covering the slice (lane l words l*sizeof(T) +
-    // i, lane 31 one more), and staged8 shifts by the row's misalignment.
-    // Words that straddle an end of the row go byte by byte, zero outside it.
+    // 16-byte-aligned chunks covering the slice (uint8: 17 chunks, lanes
+    // 0..16; uint16: 33 chunks, lane l chunk l and lane 0 chunk 32), and
+    // staged8 shifts by the row's misalignment.  Pieces that lie wholly past
+    // the row are zero-filled here; pieces that straddle an end of the row
+    // are left for the pass below, which loads their bytes one row per lane.
+    constexpr int NCH = kSliceCols * (int)sizeof(T) / 16 + 1;
     for (int r = 0; r < nr; ++r) {
         unsigned char *drow = tile + r * RB;
         const char *row = a.img + (y0 + r) * a.pitch;
@@ -426,22 +548,53 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
             if (x + 8 <= a.cols) {
                 if (sizeof(T) == 1) cp_async8(dst, src);
                 else cp_async16(dst, src);
-            } else {
+            } else if (x >= a.cols) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k) dst[k] = (x + k < a.cols) ? src[k] : (T)0;
+                for (int k = 0; k < 8; ++k) dst[k] = (T)0;
             }
         } else {
             const int m = mis(r);
-            const int nw = (int)sizeof(T) + (lane == 31 ? 1 : 0);
-            for (int i = 0; i < nw; ++i) {
-                const int k = lane * (int)sizeof(T) + i;
-                const int64_t off = xb - m + 8 * k;           // word's offset in the row
-                unsigned char *d = drow + 8 * k;
-                if (off >= 0 && off + 8 <= rowbytes) {
-                    cp_async8(d, row + off);
-                } else {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+            for (int i = 0; i < (NCH + 31) / 32; ++i) {
+                const int k = lane + 32 * i;                  // chunk index
+                if (k >= NCH) break;
+                const int64_t off = xb - m + 16 * k;          // chunk's offset in the row
+                uint4 *d = reinterpret_cast<uint4 *>(drow + 16 * k);
+                if (off >= 0 && off + 16 <= rowbytes) cp_async16(d, row + off);
+                else if (off >= rowbytes) *d = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+    }
+    // Pieces that straddle an end of a row: lane l fills rows l, l+32, ...,
+    // so their byte loads overlap across rows instead of costing one round
+    // trip per row.  They occur only in the first slice (row start) and in
+    // the last two (the row end; the second-to-last slice's extra chunk
+    // reaches up to 15 bytes into the last slice).
+    if (s == 0 || s + 2 >= a.nsx) {
+        for (int r = lane; r < nr; r += 32) {
+            unsigned char *drow = tile + r * RB;
+            const char *row = a.img + (y0 + r) * a.pitch;
+            if (VEC) {
+                const int64_t xl = (a.cols - s * kSliceCols) & ~(int64_t)7;   // partial lane's x
+                if (s == a.nsx - 1 && (a.cols & 7)) {
+                    T *dst = reinterpret_cast<T *>(drow) + xl;
+                    const T *src = reinterpret_cast<const T *>(row) + s * kSliceCols + xl;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        dst[k] = (s * kSliceCols + xl + k < a.cols) ? src[k] : (T)0;
+                }
+            } else {
+                const int64_t off0 = xb - mis(r);              // offset of chunk 0
+                const int64_t kend = (rowbytes - off0) / 16;   // chunk holding the row's end
+                const bool end_cut = kend < NCH && (rowbytes - off0) % 16 != 0;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int64_t k = e == 0 ? 0 : kend;
+                    if (e == 0 ? off0 >= 0 : (!end_cut || (kend == 0 && off0 < 0))) continue;
+                    const int64_t off = off0 + 16 * k;
+                    unsigned char *d = drow + 16 * k;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
                         const int64_t o = off + j;
                         d[j] = (o >= 0 && o < rowbytes) ? (unsigned char)row[o] : 0u;
                     }
@@ -489,100 +642,11 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
         for (int k = 0; k < 8; ++k) { cs[k] = c32[k]; cq[k] = cqa[k]; }
     }
 
-    // Vertical: publish the column sums, look back up the slice for V.
-    uint64_t vs[8] = {0, 0, 0, 0, 0, 0, 0, 0}, vq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint64_t *inv = a.inc_v + (size_t)t * 512 + lane * 8;
-    if (b > 0) {
-        uint64_t *ag = a.agg_v + (size_t)t * 512 + lane * 8;
-#pragma unroll
-        for (int k = 0; k < 8; k += 2) {
-            *reinterpret_cast<ulonglong2 *>(ag + k) = make_ulonglong2(cs[k], cs[k + 1]);
-            if (WQ)
-                *reinterpret_cast<ulonglong2 *>(ag + 256 + k) = make_ulonglong2(cq[k], cq[k + 1]);
-        }
-        publish(a.flag_v + t, kAgg);
-        for (int64_t bb = b - 1; bb >= 0; --bb) {
-            const int64_t u = bb * a.nsx + s;
-            const uint32_t f = wait_flag(a.flag_v + u, err);
-            if (!f) return false;
-            const uint64_t *src = (f == kInc ? a.inc_v : a.agg_v) + (size_t)u * 512 + lane * 8;
-#pragma unroll
-            for (int k = 0; k < 8; k += 2) {
-                const ulonglong2 v2 = __ldcg(reinterpret_cast<const ulonglong2 *>(src + k));
-                vs[k] += v2.x;
-                vs[k + 1] += v2.y;
-                if (WQ) {
-                    const ulonglong2 z = __ldcg(reinterpret_cast<const ulonglong2 *>(src + 256 + k));
-                    vq[k] += z.x;
-                    vq[k + 1] += z.y;
-                }
-            }
-            if (f == kInc) break;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-        *reinterpret_cast<ulonglong2 *>(inv + k) =
-            make_ulonglong2(vs[k] + cs[k], vs[k + 1] + cs[k + 1]);
-        if (WQ)
-            *reinterpret_cast<ulonglong2 *>(inv + 256 + k) =
-                make_ulonglong2(vq[k] + cq[k], vq[k + 1] + cq[k + 1]);
-    }
+    // Publish, look back, publish: V (as K + V* prefix), row carries, K.
+    uint64_t vs[8], vq[8], lr_s[RPL], lr_q[RPL];
+    if (!lookback_tile<WQ, TH>(a, t, b, s, cs, cq, rs_s, rs_q, err, vs, vq, lr_s, lr_q))
+        return false;
 
-    // Horizontal record = (row sums, total of V over the slice); published
-    // with the inclusive vertical record (as inclusive when s == 0).
-    uint64_t vt_s = 0, vt_q = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) { vt_s += vs[k]; vt_q += vq[k]; }
-    vt_s = warp_sum(vt_s);
-    if (WQ) vt_q = warp_sum(vt_q);
-    uint64_t lr_s[RPL], lr_q[RPL], K_s = 0, K_q = 0;
-#pragma unroll
-    for (int j = 0; j < RPL; ++j) { lr_s[j] = 0; lr_q[j] = 0; }
-    {
-        uint64_t *rec = (s > 0 ? a.agg_h : a.inc_h) + (size_t)t * HREC;
-#pragma unroll
-        for (int j = 0; j < RPL; ++j) {
-            rec[lane + 32 * j] = rs_s[j];
-            if (WQ) rec[TH + lane + 32 * j] = rs_q[j];
-        }
-        if (lane == 0) { rec[2 * TH] = vt_s; rec[2 * TH + 1] = vt_q; }
-        publish(a.flag_v + t, kInc, a.flag_h + t, s > 0 ? kAgg : kInc);
-    }
-    if (s > 0) {
-        for (int64_t ss = s - 1; ss >= 0; --ss) {
-            const int64_t u = b * a.nsx + ss;
-            const uint32_t f = wait_flag(a.flag_h + u, err);
-            if (!f) return false;
-            const uint64_t *src = (f == kInc ? a.inc_h : a.agg_h) + (size_t)u * HREC;
-#pragma unroll
-            for (int j = 0; j < RPL; ++j) {
-                lr_s[j] += __ldcg(src + lane + 32 * j);
-                if (WQ) lr_q[j] += __ldcg(src + TH + lane + 32 * j);
-            }
-            K_s += __ldcg(src + 2 * TH);
-            if (WQ) K_q += __ldcg(src + 2 * TH + 1);
-            if (f == kInc) break;
-        }
-        uint64_t *in = a.inc_h + (size_t)t * HREC;
-#pragma unroll
-        for (int j = 0; j < RPL; ++j) {
-            in[lane + 32 * j] = lr_s[j] + rs_s[j];
-            if (WQ) in[TH + lane + 32 * j] = lr_q[j] + rs_q[j];
-        }
-        if (lane == 0) { in[2 * TH] = K_s + vt_s; in[2 * TH + 1] = K_q + vt_q; }
-        publish(a.flag_h + t, kInc);
-    }
-
-    // Scan the staged tile: S = K + H[y] + V*[x] + lp.  vs/vq become K + V*.
-#pragma unroll
-    for (int k = 1; k < 8; ++k) { vs[k] += vs[k - 1]; if (WQ) vq[k] += vq[k - 1]; }
-    {
-        const uint64_t is = warp_incl_scan(vs[7], lane), es = is - vs[7];
-        const uint64_t iq = WQ ? warp_incl_scan(vq[7], lane) : 0, eq = iq - vq[7];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) { vs[k] += es + K_s; if (WQ) vq[k] += eq + K_q; }
-    }
     // Rows go in pairs: the two rows' prefix and warp-scan chains are
     // independent, which gives the scheduler two chains to interleave.
     uint32_t cp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -645,6 +709,122 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     __syncwarp();     // the tile buffer is reused by the next ticket
     return true;
 }
+
+// Process tile t of one image (single pass) without staging it in shared
+// memory: the reduction reads the tile's rows from global memory (PF rows in
+// flight), the look-back is the same as above, and the scan reads the rows
+// again (mostly from L2, which still holds them).  Shared memory per warp is
+// the output ring alone, so more warps fit on an SM.  Returns false if a
+// wait gave up.
+template <typename T, bool WQ, bool VEC, int TH>
+__device__ __forceinline__ bool onepass_tile_direct(const TileCtx &a, uint32_t t, uint32_t *err,
+                                                    WarpRes &w)
+{
+    using QA = typename QAcc<T>::type;
+    constexpr int RPL = TH / 32;
+    constexpr int PF = 8;                              // rows in flight in the reduction
+    const int lane = threadIdx.x & 31;
+    const int64_t b = t / a.nsx, s = t % a.nsx;
+    const int64_t y0 = b * TH;
+    const int nr = (int)min((int64_t)TH, a.rows - y0);
+    const int64_t x = s * kSliceCols + lane * kPxPerLane;
+    auto load = [&](int r) -> Raw8<T> {
+        if (r < nr) return load_raw8<T, VEC>(a.img, a.pitch, y0 + r, x, a.cols);
+        Raw8<T> z;
+#pragma unroll
+        for (int i = 0; i < (int)sizeof(T) * 2; ++i) z.w[i] = 0;
+        return z;
+    };
+
+    // Reduce: column sums (8 per lane), row sums (lane keeps rows lane + 32 j).
+    uint64_t cs[8], cq[8];
+    uint64_t rs_s[RPL], rs_q[RPL];
+    {
+        uint32_t c32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        Raw8<T> q[PF];                                 // rows r .. r+PF-1, shifted along
+#pragma unroll
+        for (int i = 0; i < PF; ++i) q[i] = load(i);
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            rs_s[j] = 0;
+            rs_q[j] = 0;
+            const int rend = min(nr, 32 * (j + 1));
+            for (int r = 32 * j; r < rend; ++r) {
+                uint32_t px[8];
+                unpack8<T>(q[0], px);
+#pragma unroll
+                for (int i = 0; i + 1 < PF; ++i) q[i] = q[i + 1];
+                q[PF - 1] = load(r + PF);
+                uint32_t rsum = 0;
+                QA rq = 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    c32[k] += px[k];
+                    rsum += px[k];
+                    if (WQ) {
+                        const QA p2 = (QA)px[k] * (QA)px[k];
+                        cqa[k] += p2;
+                        rq += p2;
+                    }
+                }
+                const uint64_t row_s = warp_sum(rsum);
+                const uint64_t row_q = WQ ? (uint64_t)warp_sum(rq) : 0;
+                if ((r & 31) == lane) { rs_s[j] = row_s; rs_q[j] = row_q; }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { cs[k] = c32[k]; cq[k] = cqa[k]; }
+    }
+
+    uint64_t vs[8], vq[8], lr_s[RPL], lr_q[RPL];
+    if (!lookback_tile<WQ, TH>(a, t, b, s, cs, cq, rs_s, rs_q, err, vs, vq, lr_s, lr_q))
+        return false;
+
+    // Scan, reading the rows again (two in flight): S = K + H[y] + V*[x] + lp.
+    uint32_t cp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t H_s = 0, H_q = 0;
+    const int c1 = (int)(s * (kSliceCols / 16));
+    Raw8<T> pa = load(0), pb = load(1);
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const uint64_t ls = lr_s[j], lq = lr_q[j];
+        const int rend = min(nr, 32 * (j + 1));
+        for (int r = 32 * j; r < rend; ++r) {
+            uint32_t px[8];
+            unpack8<T>(pa, px);
+            pa = pb;
+            pb = load(r + 2);
+            H_s += __shfl_sync(kFull, ls, r & 31);
+            if (WQ) H_q += __shfl_sync(kFull, lq, r & 31);
+            uint32_t lp[8];
+            QA lq8[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                cp[k] += px[k];
+                lp[k] = cp[k] + (k ? lp[k - 1] : 0u);
+                if (WQ) {
+                    cqa[k] += (QA)px[k] * (QA)px[k];
+                    lq8[k] = cqa[k] + (k ? lq8[k - 1] : (QA)0);
+                }
+            }
+            const uint32_t is = warp_incl_scan(lp[7], lane);
+            const uint64_t base_s = H_s + (uint64_t)(is - lp[7]);
+            uint64_t base_q = 0;
+            if (WQ) {
+                const QA iq = warp_incl_scan(lq8[7], lane);
+                base_q = H_q + (uint64_t)(iq - lq8[7]);
+            }
+            emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_s, vs, lp, base_q, vq, lq8, a.tmS, a.tmQ,
+                             c1, (int)(y0 + r), w.pol);
+        }
+    }
+    return true;
+}
+
+// Shared-memory bytes per warp of the direct tile routine: the ring alone.
+constexpr int direct_warp_bytes() { return kRing * 2 * kRowBytes; }
 
 // Shared-memory bytes per warp of the single-pass tile routine.
 template <typename T, int TH>

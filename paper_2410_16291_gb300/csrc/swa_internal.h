@@ -32,6 +32,7 @@ struct BuildPlan {
     // scratch layout (byte offsets inside one allocation)
     int64_t off_err, off_cs, off_rs, off_bt, off_stat, off_ticket, scratch_bytes;
     bool twopass;
+    bool direct;          // single pass reading the tile twice instead of staging it
 };
 
 struct Handle {

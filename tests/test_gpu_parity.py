@@ -98,6 +98,23 @@ def test_tables_pitched_and_unaligned(dtype, pad, offset, twopass):
     sat.free()
 
 
+# Widths whose last column slice (256 pixels) holds 1..17 pixels, and the
+# slice before it ending near a 16-byte boundary: the staging copies the
+# 16-byte-aligned chunks covering each slice, so the chunks that straddle a
+# row's start or end (first, second-to-last and last slices) and the zero
+# fill past the row are exercised for every misalignment of the row start.
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("tail", [1, 2, 7, 8, 9, 15, 16, 17])
+@pytest.mark.parametrize("pad,offset", [(0, 0), (1, 1), (3, 2), (5, 3), (8, 1)])
+@pytest.mark.parametrize("twopass", [False, True])
+def test_tables_row_ends_every_alignment(dtype, tail, pad, offset, twopass):
+    img = rand_img(67, 2 * 256 + tail, dtype)
+    dev = to_device(img, pad_cols=pad, offset_px=offset)
+    sat = swa.build_sat(dev, with_sq=True, twopass=twopass)
+    check_tables(sat, img)
+    sat.free()
+
+
 def test_sum_only_table_has_no_q():
     img = rand_img(200, 333, np.uint8)
     sat = swa.build_sat(to_device(img), with_sq=False)
