@@ -16,6 +16,9 @@ definitions and the paper sections they follow):
 - ``window_one``     one window by the definition (sampled checks at any size)
 - ``window_sat_rows`` integral-image SWA for selected output rows
 - ``stats_from_moments`` mean and population std from exact integer moments
+- ``count_brute``    threshold count map by the definition (pixels > thr per
+                     window, their fraction and the indicator's std)
+- ``count_sat``      the same through the indicator image's tables
 """
 from __future__ import annotations
 
@@ -63,6 +66,8 @@ def _load():
         lib.oracle_sat_rows.argtypes = [vp, i64, i64, i64, ci, vp, i64, vp, vp]
         lib.oracle_window_one.argtypes = [vp, i64, i64, i64, ci, i64, i64, i64, i64,
                                           P(u64), P(u64), P(dbl), P(dbl)]
+        lib.oracle_count_brute.argtypes = [vp, i64, i64, i64, ci, u64, i64, i64, i64, i64,
+                                           vp, vp, vp, i64]
         for f in (lib.oracle_window_brute, lib.oracle_window_sliding):
             f.argtypes = [vp, i64, i64, i64, ci, i64, i64, i64, i64, vp, vp, vp, i64]
         lib.oracle_window_sat.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, i64,
@@ -226,3 +231,24 @@ def total(img):
     _check(_load().oracle_total(img.ctypes.data, r, c, img.strides[0], dt,
                                 ctypes.byref(s), ctypes.byref(q)), "total")
     return s.value, q.value
+
+
+def count_brute(img, thr, wh, ww, sy=1, sx=1, outputs=("sum", "mean", "std")):
+    """Threshold count map by the definition: per window the number of pixels
+    > thr ("sum"), their fraction ("mean") and the std of the 0/1 indicator."""
+    img, dt = _img(img)
+    r, c = img.shape
+    R, C = window_shape(r, c, wh, ww, sy, sx)
+    s, m, d = _outputs(R, C, outputs)
+    _check(_load().oracle_count_brute(img.ctypes.data, r, c, img.strides[0], dt, int(thr), wh,
+                                      ww, sy, sx, _p(s), _p(m), _p(d), C), "count_brute")
+    return {k: v for k, v in (("sum", s), ("mean", m), ("std", d)) if v is not None}
+
+
+def count_sat(img, thr, windows, outputs=("sum", "mean", "std")):
+    """Threshold count maps for several windows through the tables of the
+    0/1 indicator image (img > thr); its squared values are the values, so
+    its S table serves as Q as well."""
+    ind = (np.asarray(img) > thr).astype(np.uint8)
+    S, _ = sat(ind, with_sq=False)
+    return [window_sat(S, S, wh, ww, sy, sx, outputs=outputs) for wh, ww, sy, sx in windows]

@@ -369,3 +369,36 @@ void oracle_stats_bulk(const uint64_t *n, const uint64_t *sw, const uint64_t *qw
     for (int64_t i = 0; i < count; ++i)
         oracle_stats_from_moments(n[i], sw[i], qw[i], &mean[i], &std[i]);
 }
+
+/*
+ * Threshold count map (the "additional SWA algorithms" of Section V, for
+ * cluster calling): for every valid window, the number of pixels strictly
+ * greater than `thr`, by the definition (a double loop over the window).
+ * frac = (double)count / (double)n is the fraction of such pixels and std the
+ * population standard deviation of the window's 0/1 indicator values (its
+ * squared values equal the values, so Qw = Sw = count).  Outputs are R x C
+ * with leading dimension ld; any output pointer may be NULL.
+ */
+int oracle_count_brute(const void *img, int64_t rows, int64_t cols, int64_t pitch,
+                       int dtype, uint64_t thr, int64_t wh, int64_t ww, int64_t sy,
+                       int64_t sx, uint64_t *count, double *frac, double *std, int64_t ld)
+{
+    int64_t R, C;
+    if (!args_ok(img, rows, cols, pitch, dtype)) return E_ARG;
+    if (oracle_window_shape(rows, cols, wh, ww, sy, sx, &R, &C) != OK) return E_ARG;
+    if (ld < C) return E_ARG;
+    const uint64_t n = (uint64_t)wh * (uint64_t)ww;
+    for (int64_t i = 0; i < R; ++i)
+        for (int64_t j = 0; j < C; ++j) {
+            uint64_t c = 0;
+            for (int64_t y = i * sy; y < i * sy + wh; ++y)
+                for (int64_t x = j * sx; x < j * sx + ww; ++x)
+                    c += pix(img, pitch, dtype, y, x) > thr ? 1u : 0u;
+            double m, d;
+            oracle_stats_from_moments(n, c, c, &m, &d);
+            if (count) count[i * ld + j] = c;
+            if (frac) frac[i * ld + j] = m;
+            if (std) std[i * ld + j] = d;
+        }
+    return OK;
+}
