@@ -64,6 +64,9 @@ def parse():
                     help="custom image RxC (profiling cases), e.g. 8192x8192")
     ap.add_argument("--dtype", default="u8", choices=["u8", "u16"],
                     help="pixel type of a --shape image")
+    ap.add_argument("--threshold", type=int, default=None,
+                    help="build the count table of pixels > THRESHOLD instead of S and Q "
+                         "(windows then give count / fraction / indicator std)")
     ap.add_argument("--windows", default="",
                     help="custom windows w/stride list, e.g. 100/1,256/16")
     return ap.parse_args()
@@ -299,11 +302,14 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def config_of(im, windows):
+def config_of(im, windows, threshold=None):
     return {"workload": "%dx%d %s synthetic microscopy image, %d clusters" % (
         im.rows, im.cols, im.dtype, im.n_clusters),
         "windows": ["%dx%d/s%d" % (w[0], w[1], w[2]) for w in windows],
-        "outputs": "sum,mean,std", "tables": "S and Q, uint64",
+        "outputs": ("count,fraction,std of pixels > %d" % threshold if threshold is not None
+                    else "sum,mean,std"),
+        "tables": ("count table of pixels > %d, uint64" % threshold if threshold is not None
+                   else "S and Q, uint64"),
         "l2": "inputs larger than L2 (image %.2f GB, tables %.1f GB)" % (
             im.pixels * (2 if im.dtype == "u16" else 1) / 1e9, 16 * im.pixels / 1e9)}
 
@@ -341,7 +347,10 @@ def run_ours(args, rank, world, local_rank):
     n_out = sum(R * C for R, C in shapes)
 
     def step():
-        sat = swa.build_sat(dev, with_sq=True, twopass=args.twopass)
+        if args.threshold is not None:
+            sat = swa.build_count_sat(dev, args.threshold)
+        else:
+            sat = swa.build_sat(dev, with_sq=True, twopass=args.twopass)
         sat.window_stats(windows, out=outs)
         sat.free()
 
@@ -373,6 +382,8 @@ def run_ours(args, rank, world, local_rank):
     # Per-kernel averages and the dominant kernel's roofline.
     hbm, hbm_kind = peaks()
     tables = 2
+    if args.threshold is not None:
+        tables = 1                     # the count table serves as S and Q
     build_bytes = px * ((2 if u16 else 1) + 8 * tables)
     kernels = {}
     for name, (n, tot, mx) in prof.items():
@@ -418,7 +429,7 @@ def run_ours(args, rank, world, local_rank):
 
     # End to end through swa_analyze with host buffers.
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.threshold is None:   # swa_analyze builds S and Q
         hout = [{"sum": torch.empty(s, dtype=torch.int64, pin_memory=True),
                  "mean": torch.empty(s, dtype=torch.float64, pin_memory=True),
                  "std": torch.empty(s, dtype=torch.float64, pin_memory=True)} for s in shapes]
@@ -447,7 +458,8 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "Gpx/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u64", "data": "synthetic", "config": config_of(im, windows),
+            "dtype": "u64", "data": "synthetic",
+            "config": config_of(im, windows, args.threshold),
             "sat_build_gpx_s": px / (build_ms / 1e3) / 1e9 if build_ms else None,
             "sat_build_ms": build_ms, "window_ms": win_ms,
             "window_outputs_per_s": world * n_out / (ms / 1e3),

@@ -67,8 +67,10 @@ typedef enum {
 /* Build flags. */
 enum {
     SWA_WITH_SQ = 1u,   /* also build Q, the table of squared pixels (needed for std) */
-    SWA_TWOPASS = 2u    /* read the image twice (reduce, then scan) instead of the
+    SWA_TWOPASS = 2u,   /* read the image twice (reduce, then scan) instead of the
                            single pass with decoupled look-back */
+    SWA_COUNT = 4u      /* reported by swa_sat_info for count tables
+                           (swa_build_count_sat); not a build flag */
 };
 
 /* Window output selection. */
@@ -106,6 +108,24 @@ typedef struct {
 swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols,
                          int64_t pitch_bytes, swa_dtype dtype, uint32_t flags,
                          swa_stream stream, swa_sat **out);
+
+/*
+ * Threshold count table: the summed-area table (Section II-B) of the 0/1
+ * indicator image "pixel > threshold", built in the same single pass
+ * without materialising the indicator.  Window statistics on the handle
+ * (swa_window_stats*) then give, per window, the number of pixels above the
+ * threshold (sum), their fraction (mean) and the indicator's population std
+ * (std = sqrt(p(1-p)) for fraction p) -- a count-of-positives map of the
+ * kind the paper's Section V names among additional sliding window
+ * analyses for cluster calling.  The indicator's squares equal its values,
+ * so the handle holds one uint64 table that serves as both S and Q
+ * (swa_sat_data returns the same pointer twice; swa_sat_info reports
+ * SWA_WITH_SQ | SWA_COUNT).  Entries are at most rows*cols, so there is no
+ * overflow bound.  Arguments and errors as swa_build_sat (no flags).
+ */
+swa_status swa_build_count_sat(const void *d_image, int64_t rows, int64_t cols,
+                               int64_t pitch_bytes, swa_dtype dtype, uint32_t threshold,
+                               swa_stream stream, swa_sat **out);
 
 /*
  * The single-pass build of S (and Q) without any device allocation, for

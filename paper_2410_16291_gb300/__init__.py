@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libswa.so")
 
 SWA_U8, SWA_U16 = 1, 2
 SWA_OK, SWA_EINVAL, SWA_EOVERFLOW, SWA_ENOMEM, SWA_ECUDA, SWA_ETIMEOUT = range(6)
-SWA_WITH_SQ, SWA_TWOPASS = 1, 2
+SWA_WITH_SQ, SWA_TWOPASS, SWA_COUNT = 1, 2, 4
 SWA_OUT_SUM, SWA_OUT_MEAN, SWA_OUT_STD = 1, 2, 4
 SWA_MAX_WINDOWS = 64
 SWA_HOOK_STALL_TILE0 = 1
@@ -54,6 +54,8 @@ class swa_kernel_time(ctypes.Structure):
 
 SIGNATURES = {
     "swa_build_sat": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _U32, _VP, _P(_VP)]),
+    "swa_build_count_sat": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _U32, _VP,
+                                           _P(_VP)]),
     "swa_window_shape": (ctypes.c_int, [_I64, _I64, _I64, _I64, _I64, _I64, _P(_I64), _P(_I64)]),
     "swa_window_stats": (ctypes.c_int, [_VP, _I64, _I64, _I64, _I64, _U32, _VP, _VP, _VP, _I64, _VP]),
     "swa_window_stats_multi": (ctypes.c_int, [_VP, _P(swa_window), _I32, _VP]),
@@ -268,6 +270,21 @@ def build_sat(image, with_sq=True, twopass=False, stream=None) -> SAT:
                               _dtype_code(image), flags, _stream_ptr(stream), ctypes.byref(h)),
           "swa_build_sat")
     return SAT(h.value, rows, cols, with_sq, stream)
+
+
+def build_count_sat(image, threshold, stream=None) -> SAT:
+    """The table of the 0/1 indicator "pixel > threshold" of a 2-D
+    uint8/uint16 CUDA tensor: window_stats on it gives per window the count of
+    pixels above the threshold ("sum"), their fraction ("mean") and the
+    indicator's std ("std")."""
+    assert image.is_cuda and image.dim() == 2 and image.stride(1) == 1
+    rows, cols = image.shape
+    h = _VP()
+    check(lib().swa_build_count_sat(image.data_ptr(), rows, cols,
+                                    image.stride(0) * image.element_size(), _dtype_code(image),
+                                    int(threshold), _stream_ptr(stream), ctypes.byref(h)),
+          "swa_build_count_sat")
+    return SAT(h.value, rows, cols, True, stream)
 
 
 def analyze(image, windows, outputs=("sum", "mean", "std"), out=None, stream=None,

@@ -293,7 +293,7 @@ k_scan(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
     __syncwarp();
 }
 
-template <typename T, bool WQ, bool VEC, int TH, int W, bool DIRECT>
+template <typename T, bool WQ, bool VEC, int TH, int W, bool DIRECT, bool THR>
 __global__ void __launch_bounds__(W * 32, 1)
 k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
           const __grid_constant__ CUtensorMap tmQ)
@@ -317,6 +317,7 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
     c.inc_h = a.inc_h;
     c.tmS = &tmS;
     c.tmQ = &tmQ;
+    c.thr = a.thr;
     const int64_t ntiles = a.nby * a.nsx;
     for (;;) {
         uint32_t t = 0;
@@ -325,7 +326,7 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
         if ((int64_t)t >= ntiles || *(volatile uint32_t *)a.err) break;
         if (t == 0 && a.stall_tile0) continue;
         const bool ok = DIRECT ? onepass_tile_direct<T, WQ, VEC, TH>(c, t, a.err, w)
-                               : onepass_tile<T, WQ, VEC, TH>(c, t, a.err, w);
+                               : onepass_tile<T, WQ, VEC, TH, THR>(c, t, a.err, w);
         if (!ok) break;
     }
     cp_async_wait_all();
@@ -418,7 +419,7 @@ template <typename T> constexpr int onepass_warps()
                : 16;
 }
 
-template <typename T, bool WQ, bool VEC, bool DIRECT>
+template <typename T, bool WQ, bool VEC, bool DIRECT, bool THR = false>
 swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
                           char *scratch, uint32_t *err, cudaStream_t st)
 {
@@ -441,6 +442,7 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
     a.agg_h = reinterpret_cast<uint64_t *>(scratch + p.off_rs);
     a.inc_h = a.agg_h + (size_t)p.nby * p.nsx * (2 * TH + 2);
     a.stall_tile0 = (test_hooks() & SWA_HOOK_STALL_TILE0) ? 1u : 0u;
+    a.thr = p.thr;
     CUtensorMap tmS, tmQ;
     if (!table_tensor_map(&tmS, S, p.rows, p.ld) ||
         !table_tensor_map(&tmQ, WQ ? Q : S, p.rows, p.ld)) {
@@ -450,7 +452,7 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
     }
     const size_t smem =
         1024 + (size_t)W * (DIRECT ? direct_warp_bytes() : onepass_warp_bytes<T, TH>());
-    auto kern = k_onepass<T, WQ, VEC, TH, W, DIRECT>;
+    auto kern = k_onepass<T, WQ, VEC, TH, W, DIRECT, THR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return launch_error("cudaFuncSetAttribute", e);
@@ -479,6 +481,10 @@ template <typename T>
 swa_status dispatch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
                             char *scratch, uint32_t *err, cudaStream_t st)
 {
+    if (p.count)        // indicator table: S only, staged
+        return p.vec ? launch_onepass<T, false, true, false, true>(p, img, S, Q, scratch, err, st)
+                     : launch_onepass<T, false, false, false, true>(p, img, S, Q, scratch, err,
+                                                                    st);
     if (p.direct) {
         if (p.with_q)
             return p.vec ? launch_onepass<T, true, true, true>(p, img, S, Q, scratch, err, st)
@@ -515,7 +521,8 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
     // Single-pass variant: staged tiles by default; SWA_SAT_VARIANT=direct
     // selects the variant that reads each tile twice instead (an ablation).
     const char *var = getenv("SWA_SAT_VARIANT");
-    p.direct = !p.twopass && var && strcmp(var, "direct") == 0;
+    p.count = (flags & kCountPlan) != 0;
+    p.direct = !p.twopass && !p.count && var && strcmp(var, "direct") == 0;
     p.th = p.twopass  ? kTH
            : p.direct ? (dtype == SWA_U8 ? direct_rows<uint8_t>() : direct_rows<uint16_t>())
                       : (dtype == SWA_U8 ? onepass_rows<uint8_t>() : onepass_rows<uint16_t>());

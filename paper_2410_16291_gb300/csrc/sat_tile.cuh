@@ -295,6 +295,7 @@ struct OnePass {
     uint64_t *agg_v, *inc_v;          // [tiles][2][256]
     uint64_t *agg_h, *inc_h;          // [tiles][2*TH + 2]
     uint32_t stall_tile0;             // test hook: ticket 0 publishes nothing
+    uint32_t thr;                     // count tables: pixels > thr count 1, others 0
 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
@@ -377,6 +378,7 @@ struct TileCtx {
     uint64_t *agg_v, *inc_v;          // [tiles][2][256]
     uint64_t *agg_h, *inc_h;          // [tiles][2*TH + 2]
     const CUtensorMap *tmS, *tmQ;
+    uint32_t thr;                     // with THR: the threshold of the count table
 };
 
 // Per-warp resources of the tile routine (the same for every pixel type, so
@@ -509,7 +511,7 @@ __device__ __forceinline__ bool lookback_tile(const TileCtx &a, uint32_t t, int6
 // Process tile t of one image (single pass): stage, reduce, publish, look
 // back, publish, scan, write.  Returns false if a wait gave up (the error
 // word is then set).
-template <typename T, bool WQ, bool VEC, int TH>
+template <typename T, bool WQ, bool VEC, int TH, bool THR = false>
 __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint32_t *err,
                                              WarpRes &w)
 {
@@ -529,6 +531,14 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     const uint32_t m0 = (uint32_t)reinterpret_cast<uintptr_t>(a.img + y0 * a.pitch + xb);
     const uint32_t pm = (uint32_t)a.pitch;
     auto mis = [&](int r) -> int { return VEC ? 0 : (int)((m0 + (uint32_t)r * pm) & 15u); };
+    // THR: the table of the 0/1 indicator "pixel > a.thr" (a count table).
+    auto px_of = [&](const unsigned char *row, int r, uint32_t px[8]) {
+        staged8<T, VEC>(row, lane, mis(r), px);
+        if (THR) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) px[k] = px[k] > a.thr ? 1u : 0u;
+        }
+    };
 
     // Stage the tile (rows 0..nr-1; columns past the image read as 0).  With
     // VEC every lane copies its 8 pixels with one cp.async.  Otherwise a row
@@ -620,7 +630,7 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
             const int rend = min(nr, 32 * (j + 1));
             for (int r = 32 * j; r < rend; ++r) {
                 uint32_t px[8];
-                staged8<T, VEC>(tile + r * RB, lane, mis(r), px);
+                px_of(tile + r * RB, r, px);
                 uint32_t rs = 0;
                 QA rq = 0;
 #pragma unroll
@@ -660,9 +670,9 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
         const int rend = min(nr, 32 * (j + 1));
         for (int r = 32 * j; r < rend; r += 2) {
             uint32_t pa[8], pb[8];
-            staged8<T, VEC>(tile + r * RB, lane, mis(r), pa);
+            px_of(tile + r * RB, r, pa);
             // Row r+1 < TH exists in the buffer (stale when r+1 == nr, unused).
-            staged8<T, VEC>(tile + (r + 1) * RB, lane, mis(r + 1), pb);
+            px_of(tile + (r + 1) * RB, r + 1, pb);
             // r is even, so rows r and r+1 lie in the same group of 32.
             const uint64_t ha_s = H_s + __shfl_sync(kFull, ls, r & 31);
             const uint64_t hb_s = ha_s + __shfl_sync(kFull, ls, (r + 1) & 31);

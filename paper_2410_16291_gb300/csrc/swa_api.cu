@@ -350,8 +350,16 @@ swa_status swa_trim(int64_t keep_bytes)
     return SWA_OK;
 }
 
-swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols, int64_t pitch_bytes,
-                         swa_dtype dtype, uint32_t flags, swa_stream stream, swa_sat **out)
+}  // extern "C"
+
+namespace {
+
+// Builds a handle: the tables of the image (count == false; flags as given)
+// or the table of its indicator "pixel > thr" (count == true; S only, also
+// serving as Q since the indicator's squares are the indicator).
+swa_status build_handle(const void *d_image, int64_t rows, int64_t cols, int64_t pitch_bytes,
+                        swa_dtype dtype, uint32_t flags, bool count, uint32_t thr,
+                        swa_stream stream, swa_sat **out)
 {
     if (out) *out = nullptr;
     if (!d_image || !out || rows <= 0 || cols <= 0 || (dtype != SWA_U8 && dtype != SWA_U16) ||
@@ -363,13 +371,15 @@ swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols, int64_
         set_error("uint16 images need a 2-byte aligned base and an even pitch");
         return SWA_EINVAL;
     }
-    const bool wq = flags & SWA_WITH_SQ;
-    if (!fits_u64(rows, cols, dtype, wq)) {
+    // A count table has entries <= rows*cols; otherwise the a3 bound.
+    const bool wq = !count && (flags & SWA_WITH_SQ);
+    if (!count && !fits_u64(rows, cols, dtype, wq)) {
         set_error("%lldx%lld %s image: a table entry could exceed 2^64-1", (long long)rows,
                   (long long)cols, dtype == SWA_U8 ? "uint8" : "uint16");
         return SWA_EOVERFLOW;
     }
-    BuildPlan p = make_plan(rows, cols, pitch_bytes, dtype, flags, d_image);
+    BuildPlan p = make_plan(rows, cols, pitch_bytes, dtype, count ? kCountPlan : flags, d_image);
+    p.thr = thr;
     const int64_t tbytes = p.ld * rows * 8;
     const int64_t lim = g_limit.load();
     if (lim == 0 || (lim > 0 && tbytes * (wq ? 2 : 1) + p.scratch_bytes > lim)) {
@@ -385,7 +395,7 @@ swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols, int64_
     h->cols = cols;
     h->ld = p.ld;
     h->dtype = dtype;
-    h->flags = flags;
+    h->flags = count ? (SWA_WITH_SQ | SWA_COUNT) : flags;
     h->stream = s;
     h->table_bytes = tbytes * (wq ? 2 : 1);
     cudaError_t e = cudaGetDevice(&h->device);
@@ -403,6 +413,7 @@ swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols, int64_
         if (dev_alloc(&mem, tbytes, s, &st) != cudaSuccess) goto fail;
         h->Q = static_cast<uint64_t *>(mem);
     }
+    if (count) h->Q = h->S;
     if (dev_alloc(&mem, 256, s, &st) != cudaSuccess) goto fail;
     h->d_err = static_cast<uint32_t *>(mem);
     if ((e = cudaMemsetAsync(h->d_err, 0, 256, s)) != cudaSuccess) {
@@ -424,12 +435,30 @@ swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols, int64_
 fail:
     if (scratch) dev_free(scratch, p.scratch_bytes, s);
     if (h->S) dev_free(h->S, tbytes, s);
-    if (h->Q) dev_free(h->Q, tbytes, s);
+    if (h->Q && h->Q != h->S) dev_free(h->Q, tbytes, s);
     if (h->d_err) dev_free(h->d_err, 256, s);
     if (h->use_event) cudaEventDestroy(h->use_event);
     h->tag = kFreedTag;
     delete h;
     return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols, int64_t pitch_bytes,
+                         swa_dtype dtype, uint32_t flags, swa_stream stream, swa_sat **out)
+{
+    return build_handle(d_image, rows, cols, pitch_bytes, dtype, flags, false, 0u, stream, out);
+}
+
+swa_status swa_build_count_sat(const void *d_image, int64_t rows, int64_t cols,
+                               int64_t pitch_bytes, swa_dtype dtype, uint32_t threshold,
+                               swa_stream stream, swa_sat **out)
+{
+    return build_handle(d_image, rows, cols, pitch_bytes, dtype, 0u, true, threshold, stream,
+                        out);
 }
 
 swa_status swa_window_stats(const swa_sat *sat, int64_t wh, int64_t ww, int64_t sy, int64_t sx,
@@ -514,7 +543,7 @@ void swa_free(swa_sat *sat)
     }
     const int64_t tb = h->ld * h->rows * 8;
     dev_free(h->S, tb, h->stream);
-    if (h->Q) dev_free(h->Q, tb, h->stream);
+    if (h->Q && h->Q != h->S) dev_free(h->Q, tb, h->stream);
     dev_free(h->d_err, 256, h->stream);
     cudaEventDestroy(h->use_event);
     h->tag = kFreedTag;

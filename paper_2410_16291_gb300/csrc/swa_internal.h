@@ -33,6 +33,8 @@ struct BuildPlan {
     int64_t off_err, off_cs, off_rs, off_bt, off_stat, off_ticket, scratch_bytes;
     bool twopass;
     bool direct;          // single pass reading the tile twice instead of staging it
+    bool count;           // table of the indicator "pixel > thr" (S only)
+    uint32_t thr;
 };
 
 struct Handle {
@@ -74,7 +76,10 @@ int64_t pixel_bytes(int dtype);
 // image of this dtype is below 2^64 even for an all-maximum image.
 bool fits_u64(int64_t rows, int64_t cols, int dtype, bool with_q);
 
-// SAT build (sat_build.cu).
+// SAT build (sat_build.cu).  kCountPlan (an internal flag bit): plan the
+// table of the indicator "pixel > thr" (staged single pass, S only; the
+// caller sets p.thr).
+constexpr uint32_t kCountPlan = 1u << 31;
 BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype,
                     uint32_t flags, const void *image);
 swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S,
