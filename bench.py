@@ -760,8 +760,9 @@ def run_banded(args, rank, world, local_rank):
         best = min(best, c0.elapsed_time(c1))
     h2d_gbs = host.numel() * 2 / (best / 1e3) / 1e9
     del dev
-    # Bytes over the link per step: every band's rows (halo included) in,
-    # every output out.
+    # Bytes over the link per step: the image once (a band's halo rows are
+    # copied from the previous band on the device), every output out.  The
+    # builds still process the halo rows.
     B = args.band_rows
     halo_rows = 0 if B else None       # the library picks B itself when 0
     if B:
@@ -772,7 +773,7 @@ def run_banded(args, rank, world, local_rank):
                 if ib < ie:
                     tops.append(ib * sy)
             halo_rows += b * B - min(tops) if tops else 0
-    h2d = (r + (halo_rows or 0)) * c * 2
+    h2d = r * c * 2
     d2h = 24 * n_out
     hbm, hbm_kind = peaks()
     kernels = {k: {"launches": n, "avg_ms": tot / n, "share": tot / max(1e-9, sum(

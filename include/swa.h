@@ -215,7 +215,9 @@ void swa_free(swa_sat *sat);
  * one image, evaluate n window queries, release the tables, and wait.
  * `image` and every output pointer may be host or device memory; host data
  * is staged through device memory on `stream`.  Pinned host memory gives
- * asynchronous copies.  Returns after all results are in place.
+ * asynchronous copies.  A host image of 256 MiB or more is analysed as by
+ * swa_analyze_banded with automatic bands, so that its upload overlaps the
+ * work (the results are the same).  Returns after all results are in place.
  */
 swa_status swa_analyze(const void *image, int64_t rows, int64_t cols,
                        int64_t pitch_bytes, swa_dtype dtype,

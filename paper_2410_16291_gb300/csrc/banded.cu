@@ -15,7 +15,9 @@
 //
 // Pipelining: image bands are uploaded and results downloaded on a second
 // stream, two buffers deep, so the copies of bands b+1 and b-1 overlap the
-// build and queries of band b on the caller's stream.
+// build and queries of band b on the caller's stream.  A band's halo rows
+// (the previous band's last rows) are copied from the previous band's
+// buffer on the device, so every image byte crosses the host link once.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -53,6 +55,18 @@ bool on_device(const void *p, swa_status *st)
     }
     *st = SWA_OK;
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copies `rows` rows of `pitch` bytes (a multiple of 16, 16-byte aligned
+// buffers) from src to dst in 16-byte words: the halo rows that a band
+// shares with the previous one.  (A pitched device-to-device cudaMemcpy2D of
+// the same rows measured several times slower.)
+__global__ void __launch_bounds__(256) k_copy_rows(uint4 *__restrict__ dst,
+                                                   const uint4 *__restrict__ src, int64_t words)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __ldg(src + i);
 }
 
 struct BandQuery {
@@ -210,14 +224,29 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
         bands.push_back(std::move(bd));
     }
 
-    // Device buffers: two image bands (host input), the tables and build
-    // scratch of the tallest band, two sets of output staging (host outputs).
+    // Device buffers.  Host image: the whole image when it takes at most a
+    // quarter of the free device memory (bands are uploaded into place, so
+    // a band's halo rows are already there), else two band buffers (a band's
+    // halo rows are copied from the previous band's buffer on the device).
+    // Then the tables and build scratch of the tallest band and two sets of
+    // output staging (host outputs).
     Allocs mem{s, {}};
     const int64_t dpitch = host_in ? round_up(cols * pb, 16) : pitch_bytes;
     char *img[2] = {nullptr, nullptr};
-    if (host_in)
-        for (int j = 0; j < 2; ++j)
-            if (!(img[j] = static_cast<char *>(mem.get(dpitch * max_rows, &st)))) return st;
+    bool whole = false;
+    if (host_in) {
+        size_t free_b = 0, total_b = 0;
+        cudaError_t e0 = cudaMemGetInfo(&free_b, &total_b);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMemGetInfo");
+        whole = rows * dpitch <= (int64_t)(free_b / 4);
+        if (whole) {
+            if (!(img[0] = static_cast<char *>(mem.get(dpitch * rows, &st)))) return st;
+            img[1] = img[0];
+        } else {
+            for (int j = 0; j < 2; ++j)
+                if (!(img[j] = static_cast<char *>(mem.get(dpitch * max_rows, &st)))) return st;
+        }
+    }
     const uint32_t flags = with_q ? SWA_WITH_SQ : 0u;
     // The plan's scratch grows with the row count; the tallest band's plan
     // (vector loads assumed possible) bounds every band's.
@@ -245,10 +274,14 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
             }
         }
 
-    // Copy stream and the events that order it against the compute stream.
+    // Copy stream and the events that order it against the compute stream:
+    // up[j] (band buffer j uploaded), done[j] (band results in staging j),
+    // freed[j] (band buffer j no longer read: two-buffer mode), drained[j]
+    // (staging j copied to the host).
     cudaStream_t cs = nullptr;
     cudaEvent_t up[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
-    bool done_recorded[2] = {false, false};
+    cudaEvent_t freed[2] = {nullptr, nullptr}, drained[2] = {nullptr, nullptr};
+    bool freed_recorded[2] = {false, false}, drained_recorded[2] = {false, false};
     auto cleanup = [&]() {
         if (cs) {
             cudaStreamSynchronize(cs);
@@ -257,6 +290,8 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
         for (int j = 0; j < 2; ++j) {
             if (up[j]) cudaEventDestroy(up[j]);
             if (done[j]) cudaEventDestroy(done[j]);
+            if (freed[j]) cudaEventDestroy(freed[j]);
+            if (drained[j]) cudaEventDestroy(drained[j]);
         }
     };
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -265,7 +300,9 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
     }
     for (int j = 0; j < 2; ++j)
         if ((e = cudaEventCreateWithFlags(&up[j], cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&done[j], cudaEventDisableTiming)) != cudaSuccess) {
+            (e = cudaEventCreateWithFlags(&done[j], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&freed[j], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&drained[j], cudaEventDisableTiming)) != cudaSuccess) {
             cleanup();
             return cuda_fail(e, "cudaEventCreate");
         }
@@ -276,21 +313,41 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
         return cuda_fail(e, "ordering the copy stream");
     }
 
+    // Rows [*k0, *k1) of band t that the previous band holds (two-buffer mode).
+    auto overlap = [&](size_t t, int64_t *k0, int64_t *k1) {
+        *k0 = *k1 = bands[t].L;
+        if (t == 0) return;
+        const Band &bd = bands[t], &pv = bands[t - 1];
+        const int64_t a0 = std::max(bd.L, pv.L), a1 = std::min(bd.hi, pv.hi);
+        if (a1 > a0) { *k0 = a0; *k1 = a1; }
+    };
+    int64_t uploaded = 0;                              // whole mode: rows [0, uploaded) are there
+    // Upload band t's rows that are not on the device yet (copy stream).
     auto upload = [&](size_t t) -> swa_status {
         if (!host_in) return SWA_OK;
         const int j = (int)(t & 1);
         const Band &bd = bands[t];
-        cudaError_t e2;
-        if (done_recorded[j] && (e2 = cudaStreamWaitEvent(cs, done[j], 0)) != cudaSuccess)
-            return cuda_fail(e2, "ordering an upload");
-        if ((e2 = cudaMemcpy2DAsync(img[j], (size_t)dpitch,
-                                    static_cast<const char *>(image) + bd.L * pitch_bytes,
-                                    (size_t)pitch_bytes, (size_t)(cols * pb),
-                                    (size_t)(bd.hi - bd.L), cudaMemcpyHostToDevice, cs)) !=
-                cudaSuccess ||
-            (e2 = cudaEventRecord(up[j], cs)) != cudaSuccess)
-            return cuda_fail(e2, "image band upload");
-        return SWA_OK;
+        char *base = whole ? img[0] : img[j] - bd.L * dpitch;   // + y * dpitch = row y
+        auto from_host = [&](int64_t y0, int64_t y1) -> cudaError_t {
+            if (y1 <= y0) return cudaSuccess;
+            return cudaMemcpy2DAsync(base + y0 * dpitch, (size_t)dpitch,
+                                     static_cast<const char *>(image) + y0 * pitch_bytes,
+                                     (size_t)pitch_bytes, (size_t)(cols * pb), (size_t)(y1 - y0),
+                                     cudaMemcpyHostToDevice, cs);
+        };
+        cudaError_t e2 = cudaSuccess;
+        if (whole) {
+            e2 = from_host(std::max(uploaded, bd.L), bd.hi);
+            uploaded = std::max(uploaded, bd.hi);
+        } else {
+            if (freed_recorded[j]) e2 = cudaStreamWaitEvent(cs, freed[j], 0);
+            int64_t k0, k1;
+            overlap(t, &k0, &k1);
+            if (e2 == cudaSuccess) e2 = from_host(bd.L, k0);
+            if (e2 == cudaSuccess) e2 = from_host(std::max(k1, bd.L), bd.hi);
+        }
+        if (e2 == cudaSuccess) e2 = cudaEventRecord(up[j], cs);
+        return e2 == cudaSuccess ? SWA_OK : cuda_fail(e2, "image band upload");
     };
 
     if (!bands.empty() && (st = upload(0)) != SWA_OK) {
@@ -300,10 +357,47 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
     for (size_t t = 0; t < bands.size() && st == SWA_OK; ++t) {
         const int j = (int)(t & 1);
         const Band &bd = bands[t];
+        const char *src = !host_in ? static_cast<const char *>(image) + bd.L * pitch_bytes
+                          : whole  ? img[0] + bd.L * dpitch
+                                   : img[j];
+        if (host_in) {
+            if ((e = cudaStreamWaitEvent(s, up[j], 0)) != cudaSuccess) {
+                st = cuda_fail(e, "waiting for an upload");
+                break;
+            }
+            if (!whole) {
+                // The halo rows from the previous band's buffer, on the compute
+                // stream (the previous band's work is done, so the copy has the
+                // GPU to itself); then that buffer is free for the next upload.
+                int64_t k0, k1;
+                overlap(t, &k0, &k1);
+                if (k1 > k0) {
+                    const int64_t words = (k1 - k0) * dpitch / 16;
+                    const unsigned grid =
+                        (unsigned)std::min<int64_t>((words + 255) / 256, 8192);
+                    LaunchScope ls("band_halo", s);
+                    k_copy_rows<<<grid, 256, 0, s>>>(
+                        reinterpret_cast<uint4 *>(img[j] + (k0 - bd.L) * dpitch),
+                        reinterpret_cast<const uint4 *>(img[1 - j] +
+                                                        (k0 - bands[t - 1].L) * dpitch),
+                        words);
+                    if ((e = cudaGetLastError()) != cudaSuccess) {
+                        st = cuda_fail(e, "image band halo copy");
+                        break;
+                    }
+                }
+                if ((e = cudaEventRecord(freed[1 - j], s)) != cudaSuccess) {
+                    st = cuda_fail(e, "recording a free buffer");
+                    break;
+                }
+                freed_recorded[1 - j] = true;
+            }
+        }
+        // The next band's upload overlaps this band's work.
         if (t + 1 < bands.size() && (st = upload(t + 1)) != SWA_OK) break;
-        const char *src = host_in ? img[j] : static_cast<const char *>(image) + bd.L * pitch_bytes;
-        if (host_in && (e = cudaStreamWaitEvent(s, up[j], 0)) != cudaSuccess) {
-            st = cuda_fail(e, "waiting for an upload");
+        // Staging set j held band t-2's results until their download ended.
+        if (drained_recorded[j] && (e = cudaStreamWaitEvent(s, drained[j], 0)) != cudaSuccess) {
+            st = cuda_fail(e, "waiting for a download");
             break;
         }
         const BuildPlan p = make_plan(bd.hi - bd.L, cols, dpitch, dtype, flags, src);
@@ -340,7 +434,6 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
             st = cuda_fail(e, "recording a band");
             break;
         }
-        done_recorded[j] = true;
         // Results of host-destined queries go back on the copy stream.
         bool waited = false;
         for (const BandQuery &bq : bd.q) {
@@ -362,6 +455,13 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
                     st = cuda_fail(e, "result download");
             }
             if (st != SWA_OK) break;
+        }
+        if (st == SWA_OK && waited) {
+            if ((e = cudaEventRecord(drained[j], cs)) != cudaSuccess) {
+                st = cuda_fail(e, "recording a download");
+                break;
+            }
+            drained_recorded[j] = true;
         }
     }
     // Join the copy stream back into the caller's stream, wait, and report a

@@ -36,8 +36,8 @@ struct alignas(128) BImg {
     const char *img;
     int64_t pitch, rows, cols, nby, nsx, ld;
     uint64_t *S, *Q;
-    uint32_t *flag_v, *flag_h;
-    uint64_t *agg_v, *inc_v, *agg_h, *inc_h;
+    uint32_t *flag_v, *flag_h, *flag_c;
+    uint64_t *agg_v, *inc_v, *agg_h, *inc_h, *corner;
     uint32_t tile_base, ntiles;
     int32_t dtype, vec, th;
 };
@@ -100,6 +100,8 @@ __device__ __forceinline__ bool batch_tile(const BImg &im, uint32_t t, uint32_t 
     c.nsx = im.nsx;
     c.flag_v = im.flag_v;
     c.flag_h = im.flag_h;
+    c.flag_c = im.flag_c;
+    c.corner = im.corner;
     c.agg_v = im.agg_v;
     c.inc_v = im.inc_v;
     c.agg_h = im.agg_h;
@@ -304,7 +306,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     const int64_t zero_off = off;                      // ticket, err, flags
     const int64_t off_ticket = off, off_err = off + 4;
     const int64_t off_flags = off + 256;
-    off = off_flags + 2 * 4 * tiles;
+    off = off_flags + 3 * 4 * tiles;
     const int64_t zero_bytes = off - zero_off;
     off = align256(off);
     std::vector<BImg> himg(n);
@@ -321,7 +323,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     b->cols.resize(n);
     b->stream = s;
     // Records and tables: offsets first, pointers after the allocation.
-    std::vector<int64_t> off_flag(n), off_rec_v(n), off_rec_h(n), off_tab(n);
+    std::vector<int64_t> off_flag(n), off_rec_v(n), off_rec_h(n), off_rec_c(n), off_tab(n);
     uint32_t tile_base = 0, flag_i = 0;
     for (int32_t pos = 0; pos < n; ++pos) {
         const int32_t i = order[pos];
@@ -344,11 +346,13 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
         m.tile_base = tile_base;
         tile_base += m.ntiles;
         off_flag[pos] = off_flags + 4 * (int64_t)flag_i;
-        flag_i += 2 * m.ntiles;
+        flag_i += 3 * m.ntiles;
         off_rec_v[pos] = off;
         off = align256(off + 2 * (int64_t)m.ntiles * 512 * 8);
         off_rec_h[pos] = off;
         off = align256(off + 2 * (int64_t)m.ntiles * (2 * th + 2) * 8);
+        off_rec_c[pos] = off;
+        off = align256(off + (int64_t)m.ntiles * 2 * 8);
     }
     for (int32_t pos = 0; pos < n; ++pos) {
         off_tab[pos] = off;
@@ -369,10 +373,12 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
         const int th = m.th;
         m.flag_v = reinterpret_cast<uint32_t *>(base + off_flag[pos]);
         m.flag_h = m.flag_v + m.ntiles;
+        m.flag_c = m.flag_h + m.ntiles;
         m.agg_v = reinterpret_cast<uint64_t *>(base + off_rec_v[pos]);
         m.inc_v = m.agg_v + (size_t)m.ntiles * 512;
         m.agg_h = reinterpret_cast<uint64_t *>(base + off_rec_h[pos]);
         m.inc_h = m.agg_h + (size_t)m.ntiles * (2 * th + 2);
+        m.corner = reinterpret_cast<uint64_t *>(base + off_rec_c[pos]);
         m.S = reinterpret_cast<uint64_t *>(base + off_tab[pos]);
         m.Q = m.S + m.rows * m.ld;
         if (!table_tensor_map(&m.tmS, m.S, m.rows, m.ld) ||

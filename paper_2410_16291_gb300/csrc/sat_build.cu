@@ -311,6 +311,8 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
     c.nsx = a.nsx;
     c.flag_v = a.flag_v;
     c.flag_h = a.flag_h;
+    c.flag_c = a.flag_c;
+    c.corner = a.corner;
     c.agg_v = a.agg_v;
     c.inc_v = a.inc_v;
     c.agg_h = a.agg_h;
@@ -437,10 +439,12 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
     a.ticket = reinterpret_cast<uint32_t *>(scratch + p.off_ticket);
     a.flag_v = reinterpret_cast<uint32_t *>(scratch + p.off_stat);
     a.flag_h = a.flag_v + p.nby * p.nsx;
+    a.flag_c = a.flag_h + p.nby * p.nsx;
     a.agg_v = reinterpret_cast<uint64_t *>(scratch + p.off_cs);
     a.inc_v = a.agg_v + (size_t)p.nby * p.nsx * 512;
     a.agg_h = reinterpret_cast<uint64_t *>(scratch + p.off_rs);
     a.inc_h = a.agg_h + (size_t)p.nby * p.nsx * (2 * TH + 2);
+    a.corner = reinterpret_cast<uint64_t *>(scratch + p.off_bt);
     a.stall_tile0 = (test_hooks() & SWA_HOOK_STALL_TILE0) ? 1u : 0u;
     a.thr = p.thr;
     CUtensorMap tmS, tmQ;
@@ -541,17 +545,18 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
         p.off_stat = off;
         p.off_ticket = off;
     } else {
-        // ticket, then the two flag arrays (zeroed per build), then records.
+        // ticket, then the three flag arrays (zeroed per build), then records.
         const int64_t tiles = p.nby * p.nsx;
         p.off_err = 0;
         p.off_ticket = 0;
         p.off_stat = 256;
-        off = align256(256 + 2 * tiles * 4);
+        off = align256(256 + 3 * tiles * 4);
         p.off_cs = off;                                   // vertical records
         off = align256(off + 2 * tiles * 512 * 8);
         p.off_rs = off;                                   // horizontal records
         off = align256(off + 2 * tiles * (2 * p.th + 2) * 8);
-        p.off_bt = off;
+        p.off_bt = off;                                   // corner records
+        off = align256(off + tiles * 2 * 8);
     }
     p.scratch_bytes = off;
     return p;

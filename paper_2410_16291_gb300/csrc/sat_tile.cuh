@@ -272,18 +272,16 @@ __device__ __forceinline__ void emit_row(unsigned char *ring, int &slot, const i
 // Single-pass build with decoupled look-back.  Warps take tiles in row-major
 // ticket order (an atomic counter, so every smaller ticket belongs to a warp
 // that is already running).  A warp stages its tile in shared memory, reduces
-// it, and publishes two aggregates:
+// it, and publishes two aggregates at once:
 //   vertical   (per tile column slice): the tile's 256 column sums;
-//   horizontal (per tile band): the tile's row sums and the total of the
-//              column sums above it (the corner term K of the tiles to its
-//              right).
-// It then looks back up its slice for the column carries V (summing
-// aggregates until a tile with an inclusive prefix is found), publishes its
-// own inclusive column prefix together with its horizontal aggregate, looks
-// back left along its band for the row carries LR and K the same way,
-// publishes its inclusive row prefix, and finally scans the staged tile and
-// writes S and Q through the ring.  Every wait is bounded by a time limit; on
-// expiry the warp sets the error word and all warps stop.
+//   horizontal (per tile band): the tile's row sums.
+// It then looks back up its slice for the column carries V and left along
+// its band for the row carries LR (32 predecessors' flags per round trip,
+// summing aggregates down to the nearest inclusive record), publishes its
+// inclusive records, takes the corner term K from the corner record of the
+// tile above-left, publishes its own corner, and finally scans the staged
+// tile and writes S and Q through the ring.  Every wait is bounded by a time
+// limit; on expiry the warp sets the error word and all warps stop.
 constexpr uint32_t kAgg = 1u, kInc = 2u;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
 
@@ -291,9 +289,10 @@ struct OnePass {
     const char *img;
     int64_t pitch, rows, cols, ld, nby, nsx;
     uint32_t *ticket, *err;
-    uint32_t *flag_v, *flag_h;        // [tiles]
+    uint32_t *flag_v, *flag_h, *flag_c;   // [tiles]
     uint64_t *agg_v, *inc_v;          // [tiles][2][256]
     uint64_t *agg_h, *inc_h;          // [tiles][2*TH + 2]
+    uint64_t *corner;                 // [tiles][2]
     uint32_t stall_tile0;             // test hook: ticket 0 publishes nothing
     uint32_t thr;                     // count tables: pixels > thr count 1, others 0
 };
@@ -317,25 +316,45 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Wait until *flag is non-zero in every lane; returns it, or 0 if the error
-// word is set (by this wait timing out or by another warp).
-__device__ __noinline__ uint32_t wait_flag(const uint32_t *flag, uint32_t *err)
+// Warp-wide look-back window over the chain of predecessors first, first-1,
+// ..., 0 (tile p's flag at flags[p * stride]): lane l polls predecessor
+// first - l, so one round trip reads 32 flags.  Waits (bounded) until every
+// predecessor up to the nearest inclusive one in the window has published,
+// then returns n | (inclusive << 8): add the records of predecessors first
+// .. first-n+1, the last one's inclusive record if `inclusive`, otherwise
+// n = 32 aggregates and the caller continues 32 further on.  Returns -1 if
+// the error word is set (by this wait timing out or by another warp).  The
+// warp barrier after the polls orders every lane's record loads after the
+// acquiring lane's load of the flag.
+__device__ __forceinline__ int lookback32(const uint32_t *flags, int64_t stride, int64_t first,
+                                          uint32_t *err)
 {
-    uint32_t v = ld_acquire(flag);
-    if (__all_sync(kFull, v != 0)) return __shfl_sync(kFull, v, 0);
-    const uint64_t t0 = global_ns();
+    const int lane = threadIdx.x & 31;
+    const int64_t p = first - lane;
+    const uint32_t *fp = flags + (p >= 0 ? p : 0) * stride;
+    uint64_t t0 = 0;
     unsigned ns = 64;
     for (;;) {
+        // Lanes past the chain's start count as inclusive; tile 0 of a chain
+        // always publishes an inclusive record, so they are never used.
+        const uint32_t f = p >= 0 ? ld_acquire(fp) : kInc;
+        const unsigned ready = __ballot_sync(kFull, f != 0);
+        const unsigned incm = __ballot_sync(kFull, f == kInc);
+        const unsigned need = incm ? (incm & (0u - incm)) * 2u - 1u : kFull;
+        if ((ready & need) == need) {
+            __syncwarp();
+            return incm ? (__ffs(incm) | 256) : 32;
+        }
+        if (*(volatile uint32_t *)err) return -1;
+        if (!t0) {
+            t0 = global_ns();
+        } else if (global_ns() - t0 > kWaitLimitNs) {
+            if (lane == 0) atomicOr(err, kErrTimeout);
+            __syncwarp();
+            return -1;
+        }
         __nanosleep(ns);
         if (ns < 2048) ns <<= 1;
-        v = ld_acquire(flag);
-        if (__all_sync(kFull, v != 0)) return __shfl_sync(kFull, v, 0);
-        if (*(volatile uint32_t *)err) return 0;
-        if (global_ns() - t0 > kWaitLimitNs) {
-            if ((threadIdx.x & 31) == 0) atomicOr(err, kErrTimeout);
-            __syncwarp();
-            return 0;
-        }
     }
 }
 
@@ -374,9 +393,10 @@ __device__ __forceinline__ void cp_async_wait_all()
 struct TileCtx {
     const char *img;
     int64_t pitch, rows, cols, nby, nsx;
-    uint32_t *flag_v, *flag_h;        // [tiles]
+    uint32_t *flag_v, *flag_h, *flag_c;   // [tiles]
     uint64_t *agg_v, *inc_v;          // [tiles][2][256]
     uint64_t *agg_h, *inc_h;          // [tiles][2*TH + 2]
+    uint64_t *corner;                 // [tiles][2]: S, Q at the tile's bottom-right
     const CUtensorMap *tmS, *tmQ;
     uint32_t thr;                     // with THR: the threshold of the count table
 };
@@ -391,14 +411,72 @@ struct WarpRes {
     uint64_t pol;
 };
 
+// Adds the column records (S, and Q with WQ) of the n tiles first, first-1,
+// ... of slice s above the current tile, the last one's inclusive record if
+// `inc`, two records at a time so their loads overlap.
+template <bool WQ>
+__device__ __forceinline__ void add_vertical(const TileCtx &a, int64_t first, int64_t s, int n,
+                                             bool inc, uint64_t vs[8], uint64_t vq[8])
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < n; k += 2) {
+        const bool two = k + 1 < n;
+        const int64_t u0 = (first - k) * a.nsx + s, u1 = two ? u0 - a.nsx : u0;
+        const uint64_t *s0 = (inc && k == n - 1 ? a.inc_v : a.agg_v) + (size_t)u0 * 512 + lane * 8;
+        const uint64_t *s1 =
+            (inc && k + 1 == n - 1 ? a.inc_v : a.agg_v) + (size_t)u1 * 512 + lane * 8;
+        ulonglong2 x0[4], x1[4], z0[4], z1[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x0[i] = __ldcg(reinterpret_cast<const ulonglong2 *>(s0 + 2 * i));
+            x1[i] = __ldcg(reinterpret_cast<const ulonglong2 *>(s1 + 2 * i));
+            if (WQ) {
+                z0[i] = __ldcg(reinterpret_cast<const ulonglong2 *>(s0 + 256 + 2 * i));
+                z1[i] = __ldcg(reinterpret_cast<const ulonglong2 *>(s1 + 256 + 2 * i));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            vs[2 * i] += x0[i].x + (two ? x1[i].x : 0);
+            vs[2 * i + 1] += x0[i].y + (two ? x1[i].y : 0);
+            if (WQ) {
+                vq[2 * i] += z0[i].x + (two ? z1[i].x : 0);
+                vq[2 * i + 1] += z0[i].y + (two ? z1[i].y : 0);
+            }
+        }
+    }
+}
+
+// Images at least this many column slices wide take the corner term K from
+// the tile above-left (corner mode); narrower ones from the horizontal
+// records (edge mode).  In a narrow image the tile above-left is only a few
+// tickets older, so chains of corner waits would run along the diagonals.
+constexpr int64_t kCornerMinSlices = 64;
+
 // The look-back of tile t = (b, s) after its reduction (column sums cs/cq,
-// row sums rs_s/rs_q with lane l holding rows l + 32 j): publish the
-// vertical aggregate, look back up the slice for the column carries V,
-// publish the inclusive column prefix with the horizontal aggregate (row
-// sums and the total of V: the corner term of the tiles to the right), look
-// back left for the row carries LR and the corner K, publish the inclusive
-// row prefix.  On return vs/vq hold K + V*[x] (V prefix-summed across the
-// slice) and lr_s/lr_q the row carries; false if a wait gave up.
+// row sums rs_s/rs_q with lane l holding rows l + 32 j).  It finds the column
+// carries V (looking back up the slice), the row carries LR (looking back
+// left along the band) and the corner term K, the sum of everything above
+// and to the left of the tile, in one of two ways (kCornerMinSlices):
+//
+// corner mode -- three releases:
+//   1. the vertical aggregate (column sums) and the horizontal aggregate (row
+//      sums), inclusive records directly for a chain's first tile;
+//   2. after both look-backs, the inclusive records;
+//   3. the tile's corner, the table's value at its bottom-right pixel:
+//      corner(b, s) = K + sum(V) + sum(LR) + the tile's total, with
+//      K = corner(b-1, s-1) (0 in the first band or slice).
+//   The horizontal aggregate needs nothing but the tile itself, so a band's
+//   row-carry chain never waits on the vertical look-backs of its tiles.
+// edge mode -- three releases:
+//   1. the vertical aggregate;
+//   2. after the vertical look-back, the inclusive column prefix and the
+//      horizontal aggregate: row sums and sum(V), the corner term of the
+//      tiles to the right;
+//   3. after the horizontal look-back (which also sums K), the inclusive row
+//      prefix.
+// On return vs/vq hold K + V*[x] (V prefix-summed across the slice) and
+// lr_s/lr_q the row carries; false if a wait gave up.
 template <bool WQ, int TH>
 __device__ __forceinline__ bool lookback_tile(const TileCtx &a, uint32_t t, int64_t b, int64_t s,
                                               const uint64_t cs[8], const uint64_t cq[8],
@@ -408,92 +486,135 @@ __device__ __forceinline__ bool lookback_tile(const TileCtx &a, uint32_t t, int6
                                               uint64_t lr_s[TH / 32], uint64_t lr_q[TH / 32])
 {
     constexpr int RPL = TH / 32;
-    constexpr int HREC = 2 * TH + 2;                   // horizontal record length
+    constexpr int HREC = 2 * TH + 2;                   // row sums S, Q; then sum(V) S, Q
     const int lane = threadIdx.x & 31;
-    // Vertical: publish the column sums, look back up the slice for V.
+    const bool cm = a.nsx >= kCornerMinSlices;
 #pragma unroll
     for (int k = 0; k < 8; ++k) { vs[k] = 0; vq[k] = 0; }
-    uint64_t *inv = a.inc_v + (size_t)t * 512 + lane * 8;
-    if (b > 0) {
-        uint64_t *ag = a.agg_v + (size_t)t * 512 + lane * 8;
-#pragma unroll
-        for (int k = 0; k < 8; k += 2) {
-            *reinterpret_cast<ulonglong2 *>(ag + k) = make_ulonglong2(cs[k], cs[k + 1]);
-            if (WQ)
-                *reinterpret_cast<ulonglong2 *>(ag + 256 + k) = make_ulonglong2(cq[k], cq[k + 1]);
-        }
-        publish(a.flag_v + t, kAgg);
-        for (int64_t bb = b - 1; bb >= 0; --bb) {
-            const int64_t u = bb * a.nsx + s;
-            const uint32_t f = wait_flag(a.flag_v + u, err);
-            if (!f) return false;
-            const uint64_t *src = (f == kInc ? a.inc_v : a.agg_v) + (size_t)u * 512 + lane * 8;
-#pragma unroll
-            for (int k = 0; k < 8; k += 2) {
-                const ulonglong2 v2 = __ldcg(reinterpret_cast<const ulonglong2 *>(src + k));
-                vs[k] += v2.x;
-                vs[k + 1] += v2.y;
-                if (WQ) {
-                    const ulonglong2 z = __ldcg(reinterpret_cast<const ulonglong2 *>(src + 256 + k));
-                    vq[k] += z.x;
-                    vq[k + 1] += z.y;
-                }
-            }
-            if (f == kInc) break;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-        *reinterpret_cast<ulonglong2 *>(inv + k) =
-            make_ulonglong2(vs[k] + cs[k], vs[k + 1] + cs[k + 1]);
-        if (WQ)
-            *reinterpret_cast<ulonglong2 *>(inv + 256 + k) =
-                make_ulonglong2(vq[k] + cq[k], vq[k + 1] + cq[k + 1]);
-    }
-
-    // Horizontal record = (row sums, total of V over the slice); published
-    // with the inclusive vertical record (as inclusive when s == 0).
-    uint64_t vt_s = 0, vt_q = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) { vt_s += vs[k]; vt_q += vq[k]; }
-    vt_s = warp_sum(vt_s);
-    if (WQ) vt_q = warp_sum(vt_q);
-    uint64_t K_s = 0, K_q = 0;
 #pragma unroll
     for (int j = 0; j < RPL; ++j) { lr_s[j] = 0; lr_q[j] = 0; }
-    {
-        uint64_t *rec = (s > 0 ? a.agg_h : a.inc_h) + (size_t)t * HREC;
+    uint64_t K_s = 0, K_q = 0;
+
+    auto write_vertical = [&](uint64_t *rec, bool with_v) {
+        uint64_t *r = rec + (size_t)t * 512 + lane * 8;
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            *reinterpret_cast<ulonglong2 *>(r + k) =
+                make_ulonglong2(cs[k] + (with_v ? vs[k] : 0), cs[k + 1] + (with_v ? vs[k + 1] : 0));
+            if (WQ)
+                *reinterpret_cast<ulonglong2 *>(r + 256 + k) = make_ulonglong2(
+                    cq[k] + (with_v ? vq[k] : 0), cq[k + 1] + (with_v ? vq[k + 1] : 0));
+        }
+    };
+    auto write_rows = [&](uint64_t *rec, bool with_lr) {
+        uint64_t *r = rec + (size_t)t * HREC;
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
-            rec[lane + 32 * j] = rs_s[j];
-            if (WQ) rec[TH + lane + 32 * j] = rs_q[j];
+            r[lane + 32 * j] = rs_s[j] + (with_lr ? lr_s[j] : 0);
+            if (WQ) r[TH + lane + 32 * j] = rs_q[j] + (with_lr ? lr_q[j] : 0);
         }
-        if (lane == 0) { rec[2 * TH] = vt_s; rec[2 * TH + 1] = vt_q; }
-        publish(a.flag_v + t, kInc, a.flag_h + t, s > 0 ? kAgg : kInc);
-    }
-    if (s > 0) {
-        for (int64_t ss = s - 1; ss >= 0; --ss) {
-            const int64_t u = b * a.nsx + ss;
-            const uint32_t f = wait_flag(a.flag_h + u, err);
-            if (!f) return false;
-            const uint64_t *src = (f == kInc ? a.inc_h : a.agg_h) + (size_t)u * HREC;
+    };
+    auto look_up = [&]() -> bool {                     // V, from the slice above
+        for (int64_t bb = b - 1;; bb -= 32) {
+            const int lb = lookback32(a.flag_v + s, a.nsx, bb, err);
+            if (lb < 0) return false;
+            add_vertical<WQ>(a, bb, s, lb & 255, lb >> 8, vs, vq);
+            if (lb >> 8) return true;
+        }
+    };
+    auto look_left = [&]() -> bool {                   // LR (and K in edge mode)
+        for (int64_t ss = s - 1;; ss -= 32) {
+            const int lb = lookback32(a.flag_h + b * a.nsx, 1, ss, err);
+            if (lb < 0) return false;
+            const int n = lb & 255;
+            for (int k = 0; k < n; ++k) {
+                const int64_t u = b * a.nsx + ss - k;
+                const uint64_t *src =
+                    ((lb >> 8) && k == n - 1 ? a.inc_h : a.agg_h) + (size_t)u * HREC;
 #pragma unroll
-            for (int j = 0; j < RPL; ++j) {
-                lr_s[j] += __ldcg(src + lane + 32 * j);
-                if (WQ) lr_q[j] += __ldcg(src + TH + lane + 32 * j);
+                for (int j = 0; j < RPL; ++j) {
+                    lr_s[j] += __ldcg(src + lane + 32 * j);
+                    if (WQ) lr_q[j] += __ldcg(src + TH + lane + 32 * j);
+                }
+                if (!cm) {
+                    K_s += __ldcg(src + 2 * TH);
+                    if (WQ) K_q += __ldcg(src + 2 * TH + 1);
+                }
             }
-            K_s += __ldcg(src + 2 * TH);
-            if (WQ) K_q += __ldcg(src + 2 * TH + 1);
-            if (f == kInc) break;
+            if (lb >> 8) return true;
         }
-        uint64_t *in = a.inc_h + (size_t)t * HREC;
+    };
+
+    if (cm) {
+        // 1. Both aggregates (inclusive for a chain's first tile), one release.
+        write_vertical(b > 0 ? a.agg_v : a.inc_v, false);
+        write_rows(s > 0 ? a.agg_h : a.inc_h, false);
+        publish(a.flag_v + t, b > 0 ? kAgg : kInc, a.flag_h + t, s > 0 ? kAgg : kInc);
+        // 2. Both look-backs, then the inclusive records.
+        if (b > 0) {
+            if (!look_up()) return false;
+            write_vertical(a.inc_v, true);
+        }
+        if (s > 0) {
+            if (!look_left()) return false;
+            write_rows(a.inc_h, true);
+        }
+        if (b > 0 || s > 0)
+            publish(b > 0 ? a.flag_v + t : a.flag_h + t, kInc,
+                    (b > 0 && s > 0) ? a.flag_h + t : nullptr, kInc);
+        // 3. K from the tile above-left; this tile's corner.
+        if (b > 0 && s > 0) {
+            const int64_t u = (b - 1) * a.nsx + (s - 1);
+            if (lookback32(a.flag_c + u, 1, 0, err) < 0) return false;
+            K_s = __ldcg(a.corner + 2 * u);
+            if (WQ) K_q = __ldcg(a.corner + 2 * u + 1);
+        }
+        uint64_t ps = 0, pq = 0;               // this lane's share of V + LR + the tile
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) {
-            in[lane + 32 * j] = lr_s[j] + rs_s[j];
-            if (WQ) in[TH + lane + 32 * j] = lr_q[j] + rs_q[j];
+        for (int k = 0; k < 8; ++k) { ps += vs[k] + cs[k]; pq += vq[k] + cq[k]; }
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) { ps += lr_s[j]; pq += lr_q[j]; }
+        ps = warp_sum(ps);
+        if (WQ) pq = warp_sum(pq);
+        if (lane == 0) {
+            a.corner[2 * (size_t)t] = K_s + ps;
+            a.corner[2 * (size_t)t + 1] = WQ ? K_q + pq : 0;
         }
-        if (lane == 0) { in[2 * TH] = K_s + vt_s; in[2 * TH + 1] = K_q + vt_q; }
-        publish(a.flag_h + t, kInc);
+        publish(a.flag_c + t, kInc);
+    } else {
+        // 1. The vertical aggregate.
+        if (b > 0) {
+            write_vertical(a.agg_v, false);
+            publish(a.flag_v + t, kAgg);
+            if (!look_up()) return false;
+        }
+        // 2. The inclusive column prefix and the horizontal aggregate (row
+        //    sums and sum(V)); inclusive for the band's first tile.
+        write_vertical(a.inc_v, true);
+        uint64_t vt_s = 0, vt_q = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { vt_s += vs[k]; vt_q += vq[k]; }
+        vt_s = warp_sum(vt_s);
+        if (WQ) vt_q = warp_sum(vt_q);
+        {
+            uint64_t *rec = (s > 0 ? a.agg_h : a.inc_h);
+            write_rows(rec, false);
+            if (lane == 0) {
+                rec[(size_t)t * HREC + 2 * TH] = vt_s;
+                rec[(size_t)t * HREC + 2 * TH + 1] = vt_q;
+            }
+            publish(a.flag_v + t, kInc, a.flag_h + t, s > 0 ? kAgg : kInc);
+        }
+        // 3. Row carries and K from the left; the inclusive row prefix.
+        if (s > 0) {
+            if (!look_left()) return false;
+            write_rows(a.inc_h, true);
+            if (lane == 0) {
+                a.inc_h[(size_t)t * HREC + 2 * TH] = K_s + vt_s;
+                a.inc_h[(size_t)t * HREC + 2 * TH + 1] = K_q + vt_q;
+            }
+            publish(a.flag_h + t, kInc);
+        }
     }
 
     // For the scan S = K + H[y] + V*[x] + lp: vs/vq become K + V*.

@@ -143,6 +143,9 @@ bool fits_u64(int64_t rows, int64_t cols, int dtype, bool with_q)
     return true;
 }
 
+// Host images of at least this many bytes are analysed band by band.
+constexpr int64_t kStreamedAnalyzeBytes = 256ll << 20;
+
 void set_error(const char *fmt, ...)
 {
     va_list ap;
@@ -307,8 +310,12 @@ swa_status swa_window_shape(int64_t rows, int64_t cols, int64_t wh, int64_t ww, 
                             int64_t sx, int64_t *out_r, int64_t *out_c)
 {
     if (!out_r || !out_c || rows <= 0 || cols <= 0 || wh <= 0 || ww <= 0 || sy <= 0 ||
-        sx <= 0 || wh > rows || ww > cols)
+        sx <= 0 || wh > rows || ww > cols) {
+        set_error("window %lldx%lld stride %lldx%lld does not fit a %lldx%lld image",
+                  (long long)wh, (long long)ww, (long long)sy, (long long)sx, (long long)rows,
+                  (long long)cols);
         return SWA_EINVAL;
+    }
     *out_r = (rows - wh) / sy + 1;
     *out_c = (cols - ww) / sx + 1;
     return SWA_OK;
@@ -568,6 +575,11 @@ swa_status swa_analyze(const void *image, int64_t rows, int64_t cols, int64_t pi
     if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
     const bool host_in = attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged;
     const int64_t pb = pixel_bytes(dtype);
+    // A large host image goes through the banded path: its upload then
+    // overlaps the builds and queries band by band (same results: the
+    // window sums are exact on band tables, see swa_analyze_banded).
+    if (host_in && rows * cols * pb >= kStreamedAnalyzeBytes)
+        return swa_analyze_banded(image, rows, cols, pitch_bytes, dtype, windows, n, 0, stream);
     const void *d_img = image;
     void *stage = nullptr;
     int64_t stage_bytes = 0, dpitch = pitch_bytes;

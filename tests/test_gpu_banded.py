@@ -80,3 +80,48 @@ def test_banded_repeated_calls_and_sum_only():
         res = swa.analyze(h, wl, outputs=("sum",), band_rows=40)
         want = oracle.window_brute(img, 32, 32, 1, 1, outputs=("sum",))
         np.testing.assert_array_equal(u64(res[0]["sum"]), want["sum"])
+
+
+@pytest.mark.slow
+def test_analyze_routes_large_host_images_through_bands():
+    """swa_analyze streams a host image of 256 MiB or more band by band; the
+    results equal the one-table device path bit for bit, and sampled windows
+    equal the definition."""
+    require_gpu()
+    import torch
+    r, c = 16400, 16400
+    img = _image("u8", r, c, 12)
+    wl = [(100, 100, 7, 5), (1024, 512, 16, 16)]
+    h = torch.from_numpy(img).pin_memory()
+    streamed = swa.analyze(h, wl)
+    sat = swa.build_sat(torch.from_numpy(img).cuda())
+    direct = sat.window_stats(wl)
+    for a, d in zip(streamed, direct):
+        for k in ("sum", "mean", "std"):
+            assert torch.equal(a[k], d[k].cpu()), k
+    rng = np.random.default_rng(5)
+    for (wh, ww, sy, sx), a in zip(wl, streamed):
+        R, C = a["sum"].shape
+        for i, j in zip(rng.integers(0, R, 20), rng.integers(0, C, 20)):
+            s, _, m, d = oracle.window_one(img, int(i) * sy, int(j) * sx, wh, ww)
+            assert int(u64(a["sum"][i:i + 1, j:j + 1])[0, 0]) == s
+            assert f64(a["mean"][i:i + 1, j:j + 1])[0, 0] == m
+            assert f64(a["std"][i:i + 1, j:j + 1])[0, 0] == d
+    sat.free()
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16"])
+def test_banded_device_in_host_out(dtype):
+    """Device image, pinned host outputs, many bands: the results of band t
+    are downloaded from a staging set that band t+2 reuses."""
+    require_gpu()
+    import torch
+    img = _image(dtype, 403, 389, 91)
+    d = to_device(img)
+    out = []
+    for wh, ww, sy, sx in WINDOWS:
+        R, C = swa.window_shape(*img.shape, wh, ww, sy, sx)
+        out.append({k: torch.empty((R, C), dtype=torch.int64 if k == "sum" else torch.float64,
+                                   pin_memory=True) for k in ("sum", "mean", "std")})
+    res = swa.analyze(d, WINDOWS, out=out, band_rows=4)
+    _check(img, res, WINDOWS)

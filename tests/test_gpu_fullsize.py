@@ -118,7 +118,7 @@ def test_u16_all_max_at_the_overflow_edge():
 
 def test_u16_70k_by_85k_banded():
     """70,000 x 85,000 uint16 (5.95e9 px): the squared-pixel table of the
-    whole image could overflow uint64, so the one-table path refuses it; the
+    whole image could overflow uint64, so the one-table build refuses it; the
     banded path (pinned host image in, host outputs out, 5,000-row bands)
     gives every sampled window equal to the definition, with extra samples
     on windows that end just past a band edge (their tables start in the
@@ -128,9 +128,11 @@ def test_u16_70k_by_85k_banded():
     img = synth.intensity_u16(r, c, synth.DEFAULT_SEED + 5, 50000)
     h = torch.from_numpy(img.view(np.int16)).pin_memory()
     wins = [(256, 256, 16, 16), (1024, 1024, 16, 16)]
+    dev = h.to("cuda")
     with pytest.raises(swa.SwaError) as ei:
-        swa.analyze(h, wins[:1])
+        swa.build_sat(dev)                  # the one-table build refuses it
     assert ei.value.status == swa.SWA_EOVERFLOW
+    del dev
     res = swa.analyze(h, wins, band_rows=B)
     for (wh, ww, sy, sx), got in zip(wins, res):
         R, C = got["sum"].shape

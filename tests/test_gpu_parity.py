@@ -115,6 +115,21 @@ def test_tables_row_ends_every_alignment(dtype, tail, pad, offset, twopass):
     sat.free()
 
 
+# Images at least 64 column slices (16,384 px) wide take the single pass's
+# corner mode (the corner term from the tile above-left), narrower ones the
+# edge mode; both must give the same tables.
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("shape,pad,offset", [((129, 16384), 0, 0), ((300, 16391), 3, 1),
+                                              ((67, 20000), 0, 0), ((5, 16500), 8, 3)])
+def test_tables_corner_mode(dtype, shape, pad, offset):
+    img = rand_img(*shape, dtype)
+    sat = swa.build_sat(to_device(img, pad_cols=pad, offset_px=offset), with_sq=True)
+    S_ref, Q_ref = check_tables(sat, img)
+    check_windows(sat, S_ref, Q_ref, [(min(33, shape[0]), 1000, 4, 7), (shape[0], shape[1], 1, 1)])
+    sat.sync()
+    sat.free()
+
+
 def test_sum_only_table_has_no_q():
     img = rand_img(200, 333, np.uint8)
     sat = swa.build_sat(to_device(img), with_sq=False)
