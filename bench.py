@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="passes of the plain per-request path (workload 3)")
     ap.add_argument("--no-tune", action="store_true", help="workload 3: default batch config")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0,
@@ -433,7 +433,7 @@ def run_ours(args, rank, world, local_rank):
         hout = [{"sum": torch.empty(s, dtype=torch.int64, pin_memory=True),
                  "mean": torch.empty(s, dtype=torch.float64, pin_memory=True),
                  "std": torch.empty(s, dtype=torch.float64, pin_memory=True)} for s in shapes]
-        for _ in range(max(1, min(args.warmup, 2))):
+        for _ in range(max(3, args.warmup)):        # first calls map pool memory
             swa.analyze(host, windows, out=hout)
         torch.cuda.synchronize()
         if dist:

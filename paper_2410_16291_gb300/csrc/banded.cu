@@ -13,9 +13,9 @@
 // next band.  Device memory is bounded by about B + max(wh) rows of image
 // and tables, whatever the image height.
 //
-// Pipelining: image bands are uploaded and results downloaded on a second
-// stream, two buffers deep, so the copies of bands b+1 and b-1 overlap the
-// build and queries of band b on the caller's stream.  A band's halo rows
+// Pipelining: image bands are uploaded on one stream and results downloaded
+// on another, two buffers deep, so the copies of bands b+1 and b-1 overlap
+// the build and queries of band b on the caller's stream.  A band's halo rows
 // (the previous band's last rows) are copied from the previous band's
 // buffer on the device, so every image byte crosses the host link once.
 #include <cuda_runtime.h>
@@ -278,14 +278,15 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
     // up[j] (band buffer j uploaded), done[j] (band results in staging j),
     // freed[j] (band buffer j no longer read: two-buffer mode), drained[j]
     // (staging j copied to the host).
-    cudaStream_t cs = nullptr;
+    cudaStream_t cs = nullptr, ds = nullptr;       // uploads, downloads
     cudaEvent_t up[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
     cudaEvent_t freed[2] = {nullptr, nullptr}, drained[2] = {nullptr, nullptr};
     bool freed_recorded[2] = {false, false}, drained_recorded[2] = {false, false};
     auto cleanup = [&]() {
-        if (cs) {
-            cudaStreamSynchronize(cs);
-            cudaStreamDestroy(cs);
+        for (cudaStream_t x : {cs, ds}) {
+            if (!x) continue;
+            cudaStreamSynchronize(x);
+            cudaStreamDestroy(x);
         }
         for (int j = 0; j < 2; ++j) {
             if (up[j]) cudaEventDestroy(up[j]);
@@ -294,7 +295,8 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
             if (drained[j]) cudaEventDestroy(drained[j]);
         }
     };
-    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ds, cudaStreamNonBlocking)) != cudaSuccess) {
         cleanup();
         return cuda_fail(e, "cudaStreamCreate");
     }
@@ -306,9 +308,10 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
             cleanup();
             return cuda_fail(e, "cudaEventCreate");
         }
-    // The copy stream starts after the caller's earlier work (and the memsets).
+    // The copy streams start after the caller's earlier work (and the memsets).
     if ((e = cudaEventRecord(up[0], s)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(cs, up[0], 0)) != cudaSuccess) {
+        (e = cudaStreamWaitEvent(cs, up[0], 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ds, up[0], 0)) != cudaSuccess) {
         cleanup();
         return cuda_fail(e, "ordering the copy stream");
     }
@@ -434,11 +437,11 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
             st = cuda_fail(e, "recording a band");
             break;
         }
-        // Results of host-destined queries go back on the copy stream.
+        // Results of host-destined queries go back on the download stream.
         bool waited = false;
         for (const BandQuery &bq : bd.q) {
             if (!host_out[bq.k]) continue;
-            if (!waited && (e = cudaStreamWaitEvent(cs, done[j], 0)) != cudaSuccess) {
+            if (!waited && (e = cudaStreamWaitEvent(ds, done[j], 0)) != cudaSuccess) {
                 st = cuda_fail(e, "ordering a download");
                 break;
             }
@@ -451,24 +454,26 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
                 if ((e = cudaMemcpy2DAsync(dst, (size_t)(w.out_ld * 8),
                                            staging[(j * n + bq.k) * 3 + o], (size_t)(C[bq.k] * 8),
                                            (size_t)(C[bq.k] * 8), (size_t)(bq.ie - bq.ib),
-                                           cudaMemcpyDefault, cs)) != cudaSuccess)
+                                           cudaMemcpyDefault, ds)) != cudaSuccess)
                     st = cuda_fail(e, "result download");
             }
             if (st != SWA_OK) break;
         }
         if (st == SWA_OK && waited) {
-            if ((e = cudaEventRecord(drained[j], cs)) != cudaSuccess) {
+            if ((e = cudaEventRecord(drained[j], ds)) != cudaSuccess) {
                 st = cuda_fail(e, "recording a download");
                 break;
             }
             drained_recorded[j] = true;
         }
     }
-    // Join the copy stream back into the caller's stream, wait, and report a
+    // Join the copy streams back into the caller's stream, wait, and report a
     // device-side error of any band's build.
-    cudaEvent_t fin = up[0];
-    if ((e = cudaEventRecord(fin, cs)) == cudaSuccess) e = cudaStreamWaitEvent(s, fin, 0);
-    if (st == SWA_OK && e != cudaSuccess) st = cuda_fail(e, "joining the copy stream");
+    for (cudaStream_t x : {cs, ds}) {
+        cudaEvent_t fin = x == cs ? up[0] : up[1];
+        if ((e = cudaEventRecord(fin, x)) == cudaSuccess) e = cudaStreamWaitEvent(s, fin, 0);
+        if (st == SWA_OK && e != cudaSuccess) st = cuda_fail(e, "joining the copy streams");
+    }
     uint32_t herr = 0;
     e = cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
