@@ -438,15 +438,23 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if dist:
             td.barrier()
-        t0 = time.perf_counter()
+        # Each call returns with its results on the host.  The pinned host
+        # link's rate swings from call to call on a shared machine, so the
+        # median, min and max call are reported beside the mean.
+        times = []
         for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
             swa.analyze(host, windows, out=hout)
-        torch.cuda.synchronize()
-        et = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, device="cuda")
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        et = max_over_ranks(sum(times) / len(times), device="cuda")
         e2e = {"value": job_throughput(px, et, world) / 1e9, "unit": "Gpx/s",
                "h2d_bytes_per_step": px, "d2h_bytes_per_step": 24 * n_out,
                "ms_per_step": et * 1e3, "steps": args.e2e_steps,
-               "api": "swa_analyze (pinned host image in, pinned host results out)"}
+               "ms_median": 1e3 * statistics.median(times), "ms_min": 1e3 * min(times),
+               "ms_max": 1e3 * max(times),
+               "api": "swa_analyze (pinned host image in, pinned host results out; "
+                      "host images of 256 MiB or more stream in bands)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -733,17 +741,22 @@ def run_banded(args, rank, world, local_rank):
         td.barrier()
     l0 = swa.lib().swa_launch_count()
     swa.profile_begin()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    # Every step returns with its results on the host.  The pinned host
+    # link's rate swings from step to step on a shared machine, so the
+    # median, min and max step are reported beside the mean.
+    times = []
     for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
     prof = swa.profile_end()
     launches = swa.lib().swa_launch_count() - l0
     if dist:
         td.barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device="cuda")
+    ms = max_over_ranks(sum(times) / len(times), device="cuda")
     clk = clocks.stop() if rank == 0 else None
     # The host link alone: the best of three pinned copies of the whole
     # image, device-timed.
@@ -795,6 +808,8 @@ def run_banded(args, rank, world, local_rank):
                        "band_rows": B, "halo_rows_per_step": halo_rows,
                        "l2": "inputs larger than L2 (image 11.9 GB)"},
             "window_outputs_per_s": world * n_out / (ms / 1e3),
+            "step_ms": {"median": statistics.median(times), "min": min(times),
+                        "max": max(times)},
             "kernels": kernels,
             "host_link": {"h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                           "achieved_gbs": (h2d + d2h) / (ms / 1e3) / 1e9,
