@@ -39,7 +39,7 @@ struct alignas(128) BImg {
     uint32_t *flag_v, *flag_h, *flag_c;
     uint64_t *agg_v, *inc_v, *agg_h, *inc_h, *corner;
     uint32_t tile_base, ntiles;
-    int32_t dtype, vec, th;
+    int32_t dtype, vec, th, corner_mode;
 };
 
 struct BQuery {
@@ -102,6 +102,7 @@ __device__ __forceinline__ bool batch_tile(const BImg &im, uint32_t t, uint32_t 
     c.flag_h = im.flag_h;
     c.flag_c = im.flag_c;
     c.corner = im.corner;
+    c.corner_mode = im.corner_mode != 0;
     c.agg_v = im.agg_v;
     c.inc_v = im.inc_v;
     c.agg_h = im.agg_h;
@@ -341,6 +342,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
         m.vec = ((uintptr_t)it.image % vb == 0) && (it.pitch_bytes % vb == 0);
         m.nby = (it.rows + th - 1) / th;
         m.nsx = (it.cols + kSliceCols - 1) / kSliceCols;
+        m.corner_mode = corner_mode_for(m.nsx, it.dtype) ? 1 : 0;
         m.ld = (it.cols + kLdAlign - 1) / kLdAlign * kLdAlign;
         m.ntiles = (uint32_t)(m.nby * m.nsx);
         m.tile_base = tile_base;

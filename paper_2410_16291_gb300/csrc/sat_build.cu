@@ -320,6 +320,7 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
     c.tmS = &tmS;
     c.tmQ = &tmQ;
     c.thr = a.thr;
+    c.corner_mode = a.corner_mode != 0;
     const int64_t ntiles = a.nby * a.nsx;
     for (;;) {
         uint32_t t = 0;
@@ -447,6 +448,7 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
     a.corner = reinterpret_cast<uint64_t *>(scratch + p.off_bt);
     a.stall_tile0 = (test_hooks() & SWA_HOOK_STALL_TILE0) ? 1u : 0u;
     a.thr = p.thr;
+    a.corner_mode = p.corner ? 1u : 0u;
     CUtensorMap tmS, tmQ;
     if (!table_tensor_map(&tmS, S, p.rows, p.ld) ||
         !table_tensor_map(&tmQ, WQ ? Q : S, p.rows, p.ld)) {
@@ -532,6 +534,7 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
                       : (dtype == SWA_U8 ? onepass_rows<uint8_t>() : onepass_rows<uint16_t>());
     p.nby = (rows + p.th - 1) / p.th;
     p.nsx = (cols + kSliceCols - 1) / kSliceCols;
+    p.corner = corner_mode_for(p.nsx, dtype);
     int64_t off = 0;
     if (p.twopass) {
         p.off_err = off;
@@ -560,6 +563,16 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
     }
     p.scratch_bytes = off;
     return p;
+}
+
+bool corner_mode_for(int64_t nsx, int dtype)
+{
+    static const int64_t forced = [] {
+        const char *v = getenv("SWA_CORNER_MIN_SLICES");
+        return v && *v ? (int64_t)atoll(v) : (int64_t)0;
+    }();
+    if (forced > 0) return nsx >= forced;
+    return nsx >= (dtype == SWA_U8 ? kCornerMinSlicesU8 : kCornerMinSlicesU16);
 }
 
 swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S, uint64_t *Q,

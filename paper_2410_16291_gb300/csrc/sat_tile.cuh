@@ -295,6 +295,7 @@ struct OnePass {
     uint64_t *corner;                 // [tiles][2]
     uint32_t stall_tile0;             // test hook: ticket 0 publishes nothing
     uint32_t thr;                     // count tables: pixels > thr count 1, others 0
+    uint32_t corner_mode;             // K from corner records (else edge mode)
 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
@@ -399,6 +400,7 @@ struct TileCtx {
     uint64_t *corner;                 // [tiles][2]: S, Q at the tile's bottom-right
     const CUtensorMap *tmS, *tmQ;
     uint32_t thr;                     // with THR: the threshold of the count table
+    bool corner_mode;                 // K from corner records (else edge mode)
 };
 
 // Per-warp resources of the tile routine (the same for every pixel type, so
@@ -451,7 +453,11 @@ __device__ __forceinline__ void add_vertical(const TileCtx &a, int64_t first, in
 // the tile above-left (corner mode); narrower ones from the horizontal
 // records (edge mode).  In a narrow image the tile above-left is only a few
 // tickets older, so chains of corner waits would run along the diagonals.
-constexpr int64_t kCornerMinSlices = 64;
+// Measured crossover on GB300 (build throughput, both modes forced): uint8
+// from 96 slices, uint16 (half as many rows per tile, so tickets pass twice
+// as fast) from 128.  The build's host side decides and passes the mode in.
+constexpr int64_t kCornerMinSlicesU8 = 96;
+constexpr int64_t kCornerMinSlicesU16 = 128;
 
 // The look-back of tile t = (b, s) after its reduction (column sums cs/cq,
 // row sums rs_s/rs_q with lane l holding rows l + 32 j).  It finds the column
@@ -488,7 +494,7 @@ __device__ __forceinline__ bool lookback_tile(const TileCtx &a, uint32_t t, int6
     constexpr int RPL = TH / 32;
     constexpr int HREC = 2 * TH + 2;                   // row sums S, Q; then sum(V) S, Q
     const int lane = threadIdx.x & 31;
-    const bool cm = a.nsx >= kCornerMinSlices;
+    const bool cm = a.corner_mode;
 #pragma unroll
     for (int k = 0; k < 8; ++k) { vs[k] = 0; vq[k] = 0; }
 #pragma unroll

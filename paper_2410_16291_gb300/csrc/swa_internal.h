@@ -35,6 +35,7 @@ struct BuildPlan {
     bool direct;          // single pass reading the tile twice instead of staging it
     bool count;           // table of the indicator "pixel > thr" (S only)
     uint32_t thr;
+    bool corner;          // single pass: corner term from corner records (wide images)
 };
 
 struct Handle {
@@ -80,6 +81,10 @@ bool fits_u64(int64_t rows, int64_t cols, int dtype, bool with_q);
 // table of the indicator "pixel > thr" (staged single pass, S only; the
 // caller sets p.thr).
 constexpr uint32_t kCountPlan = 1u << 31;
+// Single-pass look-back mode for an image nsx column slices wide: corner
+// records when nsx >= the dtype's threshold (SWA_CORNER_MIN_SLICES overrides
+// both built-in values, for measurements), edge mode otherwise.
+bool corner_mode_for(int64_t nsx, int dtype);
 BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype,
                     uint32_t flags, const void *image);
 swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S,

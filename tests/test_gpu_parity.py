@@ -115,12 +115,12 @@ def test_tables_row_ends_every_alignment(dtype, tail, pad, offset, twopass):
     sat.free()
 
 
-# Images at least 64 column slices (16,384 px) wide take the single pass's
+# Images at least 128 column slices (32,768 px) wide take the single pass's
 # corner mode (the corner term from the tile above-left), narrower ones the
 # edge mode; both must give the same tables.
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
-@pytest.mark.parametrize("shape,pad,offset", [((129, 16384), 0, 0), ((300, 16391), 3, 1),
-                                              ((67, 20000), 0, 0), ((5, 16500), 8, 3)])
+@pytest.mark.parametrize("shape,pad,offset", [((129, 32768), 0, 0), ((200, 32775), 3, 1),
+                                              ((67, 40000), 0, 0), ((5, 33000), 8, 3)])
 def test_tables_corner_mode(dtype, shape, pad, offset):
     img = rand_img(*shape, dtype)
     sat = swa.build_sat(to_device(img, pad_cols=pad, offset_px=offset), with_sq=True)
