@@ -46,8 +46,21 @@ struct WinQ {
     uint64_t n;           // window area
     double n_d;
     rn::Divisor div;      // n as an invariant divisor (integer path)
-    int64_t nbx;          // blocks per output row
-    int64_t first_block;  // first block of this query in the launch
+};
+
+// Queries of a launch evaluated together: every thread computes, for each
+// query of the group, the window at its own grid position (i, j), so
+// queries with one stride read their corners from the same table rows in
+// the same sweep (a window of w = k*s rows shares its corner rows with the
+// windows k grid rows further down).  The group's grid is the union of its
+// queries' output grids; blocks walk it row by row, or in column panels of
+// `panel` blocks so that the rows a panel's sweep keeps reusing stay in L2.
+struct WinGroup {
+    int64_t R;            // rows of the union grid
+    int64_t nbx;          // blocks per union-grid row
+    int64_t first_block;  // first block of this group in the launch
+    int32_t q0, nq;       // queries q[q0, q0 + nq)
+    int32_t panel;        // blocks per column panel (0: row-major order)
 };
 
 constexpr int kQPerLaunch = 16;
@@ -55,66 +68,81 @@ constexpr int kQPerLaunch = 16;
 struct WinArgs {
     const uint64_t *S, *Q;
     int64_t ld;
-    int nq;
+    int nq, ng;
     WinQ q[kQPerLaunch];
+    WinGroup g[kQPerLaunch];
 };
 
 // Windows per thread: 4 (256 apart) where the arithmetic dominates, i.e.
 // dense column strides whose corner loads mostly hit the same sectors; 1
-// where the gather dominates (column stride >= kSparseStride: every corner
-// load touches its own sector, and more resident warps hide more latency).
+// where the gather dominates (column stride >= kSparseStride: neighbouring
+// threads' corners lie 32 bytes or more apart, each corner load touches its
+// own sector, and more resident warps hide more latency).
 constexpr int kSparseStride = 4;
 inline int wins_per_thread(int64_t sx) { return sx >= kSparseStride ? 1 : 4; }
 
-// Every block covers 256*WPT consecutive windows of one output row of one
-// query (thread t: windows t, t + 256, ... of the block, so every load and
-// store instruction stays coalesced); the query is found from the launch's
-// block offsets (at most 16 entries).  Block indices fit 32 bits.
-template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN, int WPT>
-__global__ void __launch_bounds__(256) k_windows(const __grid_constant__ WinArgs a)
+// Column panel width (blocks of 256 windows) of sparse-stride groups.  With
+// about 1,200 resident blocks a 4-block panel keeps ~300 grid rows in
+// flight; their corner rows (4 x 256 + w/s points, S and Q, one 64-byte
+// line each) stay well inside L2, while row-major order over a wide image
+// (tens of blocks per row) pushes the rows a window's top corners need out
+// of L2 before they are read.
+constexpr int kPanelBlocks = 4;
+
+// A corner of a sparse-stride window.  The default fill brings 128 bytes
+// into L2 per miss, of which such a load uses 8; a 64-byte fill halves the
+// DRAM reads once corners lie 128 bytes or more apart (one 64-byte line per
+// corner point and table), and reads the same bytes as the 128-byte fill
+// for strides of 4 to 8.  The tables are read-only while a window kernel
+// runs.
+__device__ __forceinline__ uint64_t ld_corner_sparse(const uint64_t *p)
 {
-    constexpr int kWinPerThread = WPT;
-    constexpr int kWinPerBlock = 256 * WPT;
-    const uint32_t bid = blockIdx.x;
-    int k = 0;
-#pragma unroll 1
-    while (k + 1 < a.nq && bid >= (uint32_t)a.q[k + 1].first_block) ++k;
-    const WinQ &q = a.q[k];
-    const uint32_t blk = bid - (uint32_t)q.first_block;
-    const uint32_t nbx = (uint32_t)q.nbx;
-    const uint32_t i = blk / nbx;
-    const int64_t jb = (int64_t)(blk - i * nbx) * kWinPerBlock + threadIdx.x;
-    const int64_t y0 = q.w.row0 + (int64_t)i * q.w.sy, y1 = y0 + q.w.wh - 1;
+    uint64_t v;
+    asm("ld.global.nc.L2::64B.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+template <int WPT>
+__device__ __forceinline__ uint64_t ld_corner(const uint64_t *p)
+{
+    if constexpr (WPT == 1) return ld_corner_sparse(p);
+    else return __ldg(p);
+}
+
+// The WPT windows (i, jb), (i, jb + 256), ... of one query: all corner loads
+// first (independent, so they are in flight together), then the arithmetic.
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN, int WPT>
+__device__ __forceinline__ void window_row(const WinArgs &a, const WinQ &q, int64_t i, int64_t jb)
+{
+    const int64_t y0 = q.w.row0 + i * q.w.sy, y1 = y0 + q.w.wh - 1;
     const int64_t ld = a.ld;
     const bool top = y0 > 0;
     const uint64_t *St = a.S + (y0 - 1) * ld, *Sb = a.S + y1 * ld;
     const uint64_t *Qt = a.Q + (y0 - 1) * ld, *Qb = a.Q + y1 * ld;
-    const int64_t orow = (int64_t)i * q.w.out_ld;
-    // All corner loads of the thread's windows first (independent, so they
-    // are in flight together), then the arithmetic.
-    uint64_t sw[kWinPerThread], qw[kWinPerThread];
+    const int64_t orow = i * q.w.out_ld;
+    uint64_t sw[WPT], qw[WPT];
 #pragma unroll
-    for (int m = 0; m < kWinPerThread; ++m) {
+    for (int m = 0; m < WPT; ++m) {
         const int64_t j = jb + 256 * m;
         sw[m] = 0;
         qw[m] = 0;
         if (j < q.w.C) {
             const int64_t x0 = j * q.w.sx, x1 = x0 + q.w.ww - 1;
             const bool left = x0 > 0;
-            sw[m] = __ldg(Sb + x1);
-            if (top) sw[m] -= __ldg(St + x1);
-            if (left) sw[m] -= __ldg(Sb + x0 - 1);
-            if (top && left) sw[m] += __ldg(St + x0 - 1);
+            sw[m] = ld_corner<WPT>(Sb + x1);
+            if (top) sw[m] -= ld_corner<WPT>(St + x1);
+            if (left) sw[m] -= ld_corner<WPT>(Sb + x0 - 1);
+            if (top && left) sw[m] += ld_corner<WPT>(St + x0 - 1);
             if (DO_STD) {
-                qw[m] = __ldg(Qb + x1);
-                if (top) qw[m] -= __ldg(Qt + x1);
-                if (left) qw[m] -= __ldg(Qb + x0 - 1);
-                if (top && left) qw[m] += __ldg(Qt + x0 - 1);
+                qw[m] = ld_corner<WPT>(Qb + x1);
+                if (top) qw[m] -= ld_corner<WPT>(Qt + x1);
+                if (left) qw[m] -= ld_corner<WPT>(Qb + x0 - 1);
+                if (top && left) qw[m] += ld_corner<WPT>(Qt + x0 - 1);
             }
         }
     }
 #pragma unroll
-    for (int m = 0; m < kWinPerThread; ++m) {
+    for (int m = 0; m < WPT; ++m) {
         const int64_t j = jb + 256 * m;
         if (j >= q.w.C) break;
         const int64_t o = orow + j;
@@ -135,17 +163,81 @@ __global__ void __launch_bounds__(256) k_windows(const __grid_constant__ WinArgs
     }
 }
 
+// The group of block `bid`, found from the launch's block offsets (at most
+// 16 entries).  Block indices fit 32 bits.
+__device__ __forceinline__ const WinGroup &group_of(const WinArgs &a, uint32_t bid)
+{
+    int g = 0;
+#pragma unroll 1
+    while (g + 1 < a.ng && bid >= (uint32_t)a.g[g + 1].first_block) ++g;
+    return a.g[g];
+}
+
+// Dense column strides: every group holds one query; a block covers 1,024
+// consecutive windows of one output row (thread t: windows t, t + 256,
+// t + 512, t + 768, so every load and store instruction stays coalesced).
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN>
+__global__ void __launch_bounds__(256) k_windows_dense(const __grid_constant__ WinArgs a)
+{
+    const uint32_t bid = blockIdx.x;
+    const WinGroup &G = group_of(a, bid);
+    const uint32_t blk = bid - (uint32_t)G.first_block;
+    const uint32_t nbx = (uint32_t)G.nbx;
+    const uint32_t i = blk / nbx;
+    const int64_t jb = (int64_t)(blk - i * nbx) * (256 * 4) + threadIdx.x;
+    window_row<DO_SUM, DO_MEAN, DO_STD, INT_RN, 4>(a, a.q[G.q0], i, jb);
+}
+
+// Sparse column strides: a block covers 256 consecutive positions of one
+// union-grid row of a group and evaluates each of the group's queries there
+// (one window per thread and query).
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN>
+__global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ WinArgs a)
+{
+    const uint32_t bid = blockIdx.x;
+    const WinGroup &G = group_of(a, bid);
+    const uint32_t blk = bid - (uint32_t)G.first_block;
+    const uint32_t nbx = (uint32_t)G.nbx;
+    const uint32_t pw = (uint32_t)G.panel;
+    uint32_t i, bx;
+    if (pw == 0) {
+        i = blk / nbx;
+        bx = blk - i * nbx;
+    } else {
+        // Full panels of pw blocks first (each R rows deep), then the
+        // remaining nbx mod pw columns of blocks as one narrower panel.
+        const uint32_t R = (uint32_t)G.R;
+        const uint32_t full = nbx / pw, per_panel = pw * R;
+        if (blk < full * per_panel) {
+            const uint32_t p = blk / per_panel, r = blk - p * per_panel;
+            i = r / pw;
+            bx = p * pw + (r - i * pw);
+        } else {
+            const uint32_t rest = nbx - full * pw, r = blk - full * per_panel;
+            i = r / rest;
+            bx = full * pw + (r - i * rest);
+        }
+    }
+    const int64_t jb = (int64_t)bx * 256 + threadIdx.x;
+#pragma unroll 1
+    for (int k = G.q0; k < G.q0 + G.nq; ++k) {
+        const WinQ &q = a.q[k];
+        if ((int64_t)i >= q.w.R) continue;             // uniform over the block
+        window_row<DO_SUM, DO_MEAN, DO_STD, INT_RN, 1>(a, q, i, jb);
+    }
+}
+
 template <bool A, bool B, bool C, bool I>
 void launch_one(const WinArgs &a, unsigned blocks, int wpt, cudaStream_t s)
 {
     LaunchScope ls("window_stats", s);
-    if (wpt == 1) k_windows<A, B, C, I, 1><<<blocks, 256, 0, s>>>(a);
-    else k_windows<A, B, C, I, 4><<<blocks, 256, 0, s>>>(a);
+    if (wpt == 1) k_windows_sparse<A, B, C, I><<<blocks, 256, 0, s>>>(a);
+    else k_windows_dense<A, B, C, I><<<blocks, 256, 0, s>>>(a);
 }
 
 swa_status flush(WinArgs &a, int64_t blocks, uint32_t o, bool int_rn, int wpt, cudaStream_t s)
 {
-    if (a.nq == 0 || blocks == 0) return SWA_OK;
+    if (a.ng == 0 || blocks == 0) return SWA_OK;
     if (blocks > 0x7fffffffLL) {
         set_error("window grid too large (%lld blocks)", (long long)blocks);
         return SWA_EINVAL;
@@ -174,43 +266,70 @@ swa_status flush(WinArgs &a, int64_t blocks, uint32_t o, bool int_rn, int wpt, c
 
 // Queries sharing an output selection, arithmetic path and windows per
 // thread go into one launch (up to 16 per launch); the others follow in
-// launches of their own.
+// launches of their own.  Within a launch, sparse-stride queries with the
+// same strides form one group (one sweep over their union grid); every
+// other query is a group of its own.
 swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, const WinDesc *w,
                           int n, cudaStream_t s)
 {
     bool done[SWA_MAX_WINDOWS] = {false};
+    auto int_rn_of = [&](int k) { return (uint64_t)(w[k].wh * w[k].ww) < (1ull << 32); };
     for (int k0 = 0; k0 < n; ++k0) {
         if (done[k0]) continue;
         const uint32_t o = w[k0].outputs;
-        const bool int_rn = (uint64_t)(w[k0].wh * w[k0].ww) < (1ull << 32);
+        const bool int_rn = int_rn_of(k0);
         const int wpt = wins_per_thread(w[k0].sx);
+        auto fits = [&](int k) {
+            return !done[k] && w[k].outputs == o && int_rn_of(k) == int_rn &&
+                   wins_per_thread(w[k].sx) == wpt;
+        };
         WinArgs a;
         a.S = S;
         a.Q = Q;
         a.ld = ld;
         a.nq = 0;
+        a.ng = 0;
         int64_t blocks = 0;
-        for (int k = k0; k < n; ++k) {
-            const uint64_t area = (uint64_t)(w[k].wh * w[k].ww);
-            if (done[k] || w[k].outputs != o || (area < (1ull << 32)) != int_rn ||
-                wins_per_thread(w[k].sx) != wpt)
-                continue;
-            done[k] = true;
-            const int64_t nbx = (w[k].C + 256 * wpt - 1) / (256 * wpt);
-            if (w[k].R * nbx == 0) continue;
-            WinQ &q = a.q[a.nq++];
-            q.w = w[k];
-            q.n = area;
-            q.n_d = (double)area;
-            q.div = rn::make_divisor(int_rn ? (uint32_t)area : 1u);
-            q.nbx = nbx;
-            q.first_block = blocks;
-            blocks += w[k].R * nbx;
-            if (a.nq == kQPerLaunch) {
+        for (int k1 = k0; k1 < n; ++k1) {
+            if (!fits(k1)) continue;
+            // The group led by k1: k1 and, for sparse strides, every later
+            // fitting query with its strides (at most one launch's worth).
+            int members[kQPerLaunch], m = 0;
+            int64_t R = 0, C = 0;
+            for (int k = k1; k < n && m < kQPerLaunch; ++k) {
+                if (!fits(k)) continue;
+                if (k != k1 && (wpt != 1 || w[k].sy != w[k1].sy || w[k].sx != w[k1].sx))
+                    continue;
+                done[k] = true;
+                if (w[k].R == 0 || w[k].C == 0) continue;   // nothing to evaluate
+                members[m++] = k;
+                R = w[k].R > R ? w[k].R : R;
+                C = w[k].C > C ? w[k].C : C;
+            }
+            if (m == 0) continue;
+            if (a.nq + m > kQPerLaunch || a.ng == kQPerLaunch) {
                 swa_status st = flush(a, blocks, o, int_rn, wpt, s);
                 if (st != SWA_OK) return st;
                 a.nq = 0;
+                a.ng = 0;
                 blocks = 0;
+            }
+            WinGroup &g = a.g[a.ng++];
+            g.R = R;
+            g.nbx = (C + 256 * wpt - 1) / (256 * wpt);
+            g.first_block = blocks;
+            g.q0 = a.nq;
+            g.nq = m;
+            g.panel = (wpt == 1 && g.nbx > kPanelBlocks) ? kPanelBlocks : 0;
+            blocks += R * g.nbx;
+            for (int t = 0; t < m; ++t) {
+                const int k = members[t];
+                const uint64_t area = (uint64_t)(w[k].wh * w[k].ww);
+                WinQ &q = a.q[a.nq++];
+                q.w = w[k];
+                q.n = area;
+                q.n_d = (double)area;
+                q.div = rn::make_divisor(int_rn ? (uint32_t)area : 1u);
             }
         }
         swa_status st = flush(a, blocks, o, int_rn, wpt, s);

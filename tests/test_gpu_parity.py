@@ -151,6 +151,25 @@ def test_windows_bitexact(dtype):
     sat.free()
 
 
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_windows_grouped_sparse_strides(dtype):
+    """Sparse-stride queries with equal strides are evaluated in one sweep
+    over their union grid, in column panels of 4 blocks: sizes from 1 to the
+    whole image, more same-stride queries than one launch holds (21 > 16),
+    groups with other strides in the same call, a ragged last panel."""
+    img = rand_img(613, 9000, dtype)          # stride 4: 2,250 columns = 8.8 blocks
+    sat = swa.build_sat(to_device(img))
+    S_ref, Q_ref = check_tables(sat, img)
+    windows = [(8, 8, 4, 4), (64, 64, 4, 4), (100, 36, 4, 4), (613, 40, 4, 4),
+               (613, 9000, 4, 4), (1, 1, 4, 4), (33, 33, 16, 5), (256, 512, 16, 5),
+               (5, 17, 1, 4), (12, 12, 1, 1)]
+    windows += [(3 + 5 * k, 2 + 7 * k, 5, 7) for k in range(21)]
+    check_windows(sat, S_ref, Q_ref, windows)
+    check_windows(sat, S_ref, Q_ref, windows[:4], outputs=("sum",))
+    check_windows(sat, S_ref, Q_ref, windows[6:8], outputs=("mean", "std"))
+    sat.free()
+
+
 def test_windows_closed_forms():
     """Constant image: mean exact, std exactly 0; checkerboard {0, a}, even w:
     std exactly a/2."""
