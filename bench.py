@@ -35,8 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "SAT build Gpx/s + window outputs/s, % HBM peak; served p50/p99 vs plain path"
 # Thread instructions per window (sum, mean, std; 4 windows per thread) of
 # the window kernel, from ncu on the 12,288^2 stride-1 case
-# (profiles/window_stats_12288x12288.md).
-INSTR_PER_WINDOW = 475.0
+# (profiles/window_stats_dense_12288x12288.md).
+INSTR_PER_WINDOW = 482.0
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -404,7 +404,7 @@ def run_ours(args, rank, world, local_rank):
         # kernel by instruction issue.  Peak = SMs x 4 schedulers x 32 lanes x
         # the SM clock sampled during the run; achieved = windows/s x the
         # instructions per window ncu measured for this kernel (sum, mean and
-        # std at stride 1, profiles/window_stats_12288x12288.md).
+        # std at stride 1, profiles/window_stats_dense_12288x12288.md).
         n_win = sum(R * C for R, C in shapes)
         sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
         mhz = (clk or {}).get("sm_mhz") or 2070.0
