@@ -356,8 +356,12 @@ int32_t swa_profile_end(swa_kernel_time *out, int32_t max);
 /* Test hooks (process-wide bit set, 0 = none).  SWA_HOOK_STALL_TILE0: in the
  * single-pass build the tile taken first never publishes its carries, so
  * every other tile's bounded wait expires (after about 2 s) and swa_sync
- * returns SWA_ETIMEOUT; the kernel still exits.  For failure-path tests. */
-enum { SWA_HOOK_STALL_TILE0 = 1u };
+ * returns SWA_ETIMEOUT; the kernel still exits.  For failure-path tests.
+ * SWA_HOOK_BAND_BUFFERS: swa_analyze_banded stages a host image in two band
+ * buffers (halo rows copied on the device) even when the whole image would
+ * fit, so the mode used for images larger than a quarter of the free device
+ * memory can be tested on small ones. */
+enum { SWA_HOOK_STALL_TILE0 = 1u, SWA_HOOK_BAND_BUFFERS = 2u };
 swa_status swa_set_test_hooks(uint32_t hooks);
 
 /* ABI version: major * 10000 + minor * 100 + patch. */

@@ -21,6 +21,7 @@ SWA_WITH_SQ, SWA_TWOPASS, SWA_COUNT = 1, 2, 4
 SWA_OUT_SUM, SWA_OUT_MEAN, SWA_OUT_STD = 1, 2, 4
 SWA_MAX_WINDOWS = 64
 SWA_HOOK_STALL_TILE0 = 1
+SWA_HOOK_BAND_BUFFERS = 2
 
 #: C function name -> (restype, argtypes)
 _I64, _U64, _U32, _I32, _VP = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,

@@ -108,4 +108,6 @@ def test_sat_bytes(L):
 
 def test_test_hooks_validate(L):
     assert L.swa_set_test_hooks(0) == swa.SWA_OK
-    assert L.swa_set_test_hooks(2) == swa.SWA_EINVAL
+    assert L.swa_set_test_hooks(swa.SWA_HOOK_BAND_BUFFERS) == swa.SWA_OK
+    assert L.swa_set_test_hooks(0) == swa.SWA_OK
+    assert L.swa_set_test_hooks(4) == swa.SWA_EINVAL

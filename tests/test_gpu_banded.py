@@ -42,6 +42,41 @@ def test_banded_host_in_host_out(dtype, band_rows):
     _check(img, res, WINDOWS)
 
 
+@pytest.mark.parametrize("dtype,cols,band_rows", [("u8", 733, 5), ("u8", 640, 64), ("u16", 733, 33),
+                                                  ("u8", 733, 0), ("u16", 640, 150)])
+def test_banded_two_buffer_mode(dtype, cols, band_rows):
+    """A host image staged in two band buffers (the mode for images larger
+    than a quarter of the free device memory), forced on a small image by a
+    test hook: each band's rows shared with the previous band are copied on
+    the device, the rest uploaded (linear copies when host and device rows
+    have the same pitch, pitched ones otherwise)."""
+    require_gpu()
+    import torch
+    L = swa.lib()
+    img = _image(dtype, 611, cols, 19 + band_rows)
+    h = torch.from_numpy(img.view(np.int16) if dtype == "u16" else img).pin_memory()
+    assert L.swa_set_test_hooks(swa.SWA_HOOK_BAND_BUFFERS) == 0
+    try:
+        res = swa.analyze(h, WINDOWS, band_rows=band_rows)
+    finally:
+        L.swa_set_test_hooks(0)
+    _check(img, res, WINDOWS)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16"])
+def test_banded_pitched_host_image(dtype):
+    """Host rows with padding (a column slice of a wider pinned array) go to
+    back-to-back device rows with pitched copies."""
+    require_gpu()
+    import torch
+    img = _image(dtype, 450, 519, 23)
+    wide = np.zeros((450, 530), dtype=img.dtype)
+    wide[:, 3:522] = img
+    h = torch.from_numpy(wide.view(np.int16) if dtype == "u16" else wide).pin_memory()[:, 3:522]
+    res = swa.analyze(h, WINDOWS, band_rows=40)
+    _check(img, res, WINDOWS)
+
+
 @pytest.mark.parametrize("dtype", ["u8", "u16"])
 def test_banded_device_in_device_out_pitched(dtype):
     require_gpu()
