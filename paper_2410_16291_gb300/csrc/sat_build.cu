@@ -301,7 +301,7 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     WarpRes w = DIRECT ? warp_res<T, TH>(smem_raw, direct_warp_bytes())
-                       : warp_res<T, TH>(smem_raw);
+                       : warp_res<T, TH, WQ>(smem_raw);
     TileCtx c;
     c.img = a.img;
     c.pitch = a.pitch;
@@ -415,10 +415,10 @@ constexpr int kDirectWarps = 16;
 // the shared memory of one SM holds (227 KB per block, 1 KB for alignment),
 // at most 16.  One block runs per SM.
 constexpr int kSmemPerBlock = 227 * 1024;
-template <typename T> constexpr int onepass_warps()
+template <typename T, bool WQ> constexpr int onepass_warps()
 {
-    return (kSmemPerBlock - 1024) / onepass_warp_bytes<T, onepass_rows<T>()>() < 16
-               ? (kSmemPerBlock - 1024) / onepass_warp_bytes<T, onepass_rows<T>()>()
+    return (kSmemPerBlock - 1024) / onepass_warp_bytes<T, onepass_rows<T>(), WQ>() < 16
+               ? (kSmemPerBlock - 1024) / onepass_warp_bytes<T, onepass_rows<T>(), WQ>()
                : 16;
 }
 
@@ -427,7 +427,7 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
                           char *scratch, uint32_t *err, cudaStream_t st)
 {
     constexpr int TH = DIRECT ? direct_rows<T>() : onepass_rows<T>();
-    constexpr int W = DIRECT ? kDirectWarps : onepass_warps<T>();
+    constexpr int W = DIRECT ? kDirectWarps : onepass_warps<T, WQ>();
     OnePass a;
     a.img = img;
     a.pitch = p.pitch;
@@ -457,7 +457,7 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
         return SWA_ECUDA;
     }
     const size_t smem =
-        1024 + (size_t)W * (DIRECT ? direct_warp_bytes() : onepass_warp_bytes<T, TH>());
+        1024 + (size_t)W * (DIRECT ? direct_warp_bytes() : onepass_warp_bytes<T, TH, WQ>());
     auto kern = k_onepass<T, WQ, VEC, TH, W, DIRECT, THR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

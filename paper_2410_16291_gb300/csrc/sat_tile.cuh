@@ -177,6 +177,10 @@ __device__ __forceinline__ void staged8(const unsigned char *row, int lane, int 
 constexpr int kRing = 2;                           // output row slots per warp
 constexpr int kRowBytes = kSliceCols * 8;          // one table row segment (2 KB)
 
+// Ring bytes per warp: each slot holds an S row segment, and a Q one when
+// the build writes Q.
+template <bool WQ> constexpr int ring_bytes() { return kRing * (WQ ? 2 : 1) * kRowBytes; }
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -243,7 +247,7 @@ __device__ __forceinline__ void emit_row(unsigned char *ring, int &slot, const i
                                          int c1, int y, uint64_t pol)
 {
     const int lane = threadIdx.x & 31;
-    unsigned char *rs = ring + slot * (2 * kRowBytes);
+    unsigned char *rs = ring + slot * ((WQ ? 2 : 1) * kRowBytes);
     unsigned char *rq = rs + kRowBytes;
     if (lane == 0) bulk_wait_ring();     // the slot's previous copy has read it
     __syncwarp();
@@ -961,27 +965,29 @@ __device__ __forceinline__ bool onepass_tile_direct(const TileCtx &a, uint32_t t
 }
 
 // Shared-memory bytes per warp of the direct tile routine: the ring alone.
-constexpr int direct_warp_bytes() { return kRing * 2 * kRowBytes; }
+constexpr int direct_warp_bytes() { return ring_bytes<true>(); }
 
-// Shared-memory bytes per warp of the single-pass tile routine.
-template <typename T, int TH>
+// Shared-memory bytes per warp of the single-pass tile routine (a build
+// without Q keeps a ring of S rows only, so more warps fit on an SM).
+template <typename T, int TH, bool WQ = true>
 constexpr int onepass_warp_bytes()
 {
-    return (kRing * 2 * kRowBytes + TH * tile_row_bytes<T>() + 1023) / 1024 * 1024;
+    return (ring_bytes<WQ>() + TH * tile_row_bytes<T>() + 1023) / 1024 * 1024;
 }
 
 // The warp's ring and tile inside the block's dynamic shared memory; warps
 // are `stride` bytes apart (a multiple of 1024, at least the routine's need).
-template <typename T, int TH>
+template <typename T, int TH, bool WQ = true>
 __device__ __forceinline__ WarpRes warp_res(unsigned char *smem_raw,
-                                            int stride = onepass_warp_bytes<T, TH>())
+                                            int stride = onepass_warp_bytes<T, TH, WQ>())
 {
-    static_assert(onepass_warp_bytes<T, TH>() % 1024 == 0, "ring slots stay 1024-byte aligned");
+    static_assert(onepass_warp_bytes<T, TH, WQ>() % 1024 == 0,
+                  "ring slots stay 1024-byte aligned");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned char *base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     WarpRes w;
     w.ring = base + (size_t)warp * stride;
-    w.tile = w.ring + kRing * 2 * kRowBytes;
+    w.tile = w.ring + ring_bytes<WQ>();
     w.slot = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) w.sw[j] = swz_off(lane, j);
