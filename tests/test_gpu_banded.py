@@ -77,6 +77,20 @@ def test_banded_pitched_host_image(dtype):
     _check(img, res, WINDOWS)
 
 
+@pytest.mark.parametrize("band_rows", [9, 50, 0])
+def test_banded_same_stride_queries_of_different_heights(band_rows):
+    """Sparse-stride queries with equal strides share one sweep; in a band
+    their first output rows start at different table rows (row0), so they
+    do not share corner loads.  Heights 8..200, strides 4 and 16."""
+    require_gpu()
+    import torch
+    img = _image("u8", 433, 1500, 5 + band_rows)
+    wl = [(8, 8, 4, 4), (40, 24, 4, 4), (200, 96, 4, 4), (16, 256, 16, 16), (128, 16, 16, 16)]
+    h = torch.from_numpy(img).pin_memory()
+    res = swa.analyze(h, wl, band_rows=band_rows)
+    _check(img, res, wl)
+
+
 @pytest.mark.parametrize("dtype", ["u8", "u16"])
 def test_banded_device_in_device_out_pitched(dtype):
     require_gpu()
