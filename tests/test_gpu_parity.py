@@ -170,6 +170,33 @@ def test_windows_grouped_sparse_strides(dtype):
     sat.free()
 
 
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_hand_worked_golden(dtype):
+    """The CUDA path on the hand-worked cases of tests/golden/hand_worked.txt:
+    tables and sums exact, means the correctly rounded quotient, stds within
+    2 ulp of the exact root and equal to the oracle's bit for bit."""
+    import golden_util
+    for case in golden_util.load_cases():
+        img = case["image"].astype(dtype)
+        sat = swa.build_sat(to_device(img))
+        S, Q = sat.tables()
+        if "S" in case:
+            np.testing.assert_array_equal(u64(S), case["S"])
+            np.testing.assert_array_equal(u64(Q), case["Q"])
+        S_ref, Q_ref = oracle.sat(img)
+        shapes = [w["shape"] for w in case["windows"]]
+        for w, got in zip(case["windows"], sat.window_stats(shapes)):
+            R, C = swa.window_shape(*img.shape, *w["shape"])
+            s, m, d = golden_util.expected(w, R, C)
+            np.testing.assert_array_equal(u64(got["sum"]), s)
+            np.testing.assert_array_equal(f64(got["mean"]), m)
+            g = f64(got["std"])
+            assert (np.abs(g - d) <= 2 * np.spacing(d)).all(), (case["name"], w["shape"])
+            want = oracle.window_sat(S_ref, Q_ref, *w["shape"])
+            np.testing.assert_array_equal(g, want["std"])
+        sat.free()
+
+
 def test_windows_closed_forms():
     """Constant image: mean exact, std exactly 0; checkerboard {0, a}, even w:
     std exactly a/2."""

@@ -13,6 +13,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
+import golden_util
 import oracle
 import synth
 
@@ -56,11 +57,15 @@ def test_sat_recurrence_and_total(dtype):
 
 
 def test_sat_hand_worked():
-    """A 3x3 image summed by hand."""
-    img = np.arange(1, 10, dtype=np.uint8).reshape(3, 3)
-    S, Q = oracle.sat(img)
-    np.testing.assert_array_equal(S, [[1, 3, 6], [5, 12, 21], [12, 27, 45]])
-    np.testing.assert_array_equal(Q, [[1, 5, 14], [17, 46, 91], [66, 159, 285]])
+    """The hand-worked tables of tests/golden/hand_worked.txt (Section II-B's
+    inclusive table), for both pixel types."""
+    for case in golden_util.load_cases():
+        if "S" not in case:
+            continue
+        for dt in (np.uint8, np.uint16):
+            S, Q = oracle.sat(case["image"].astype(dt))
+            np.testing.assert_array_equal(S, case["S"])
+            np.testing.assert_array_equal(Q, case["Q"])
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
@@ -149,13 +154,22 @@ def test_window_shape_rule():
 
 
 def test_windows_hand_worked():
-    """2x2 windows of the 3x3 image 1..9, by hand."""
-    img = np.arange(1, 10, dtype=np.uint8).reshape(3, 3)
-    out = oracle.window_brute(img, 2, 2, 1, 1)
-    np.testing.assert_array_equal(out["sum"], [[12, 16], [24, 28]])
-    np.testing.assert_array_equal(out["mean"], [[3.0, 4.0], [6.0, 7.0]])
-    # each window holds {a, a+1, a+3, a+4}: deviations -2, -1, 1, 2 -> var 10/4
-    np.testing.assert_array_equal(out["std"], np.full((2, 2), math.sqrt(2.5)))
+    """Every window of tests/golden/hand_worked.txt through the three window
+    algorithms: sums exact, means the correctly rounded quotient, stds within
+    2 ulp of the exact root (Section II-A's average and standard deviation)."""
+    for case in golden_util.load_cases():
+        img = case["image"].astype(np.uint8)
+        S, Q = oracle.sat(img)
+        for w in case["windows"]:
+            wh, ww, sy, sx = w["shape"]
+            R, C = oracle.window_shape(*img.shape, wh, ww, sy, sx)
+            s, m, d = golden_util.expected(w, R, C)
+            for out in (oracle.window_brute(img, wh, ww, sy, sx),
+                        oracle.window_sat(S, Q, wh, ww, sy, sx),
+                        oracle.window_sliding(img, wh, ww, sy, sx)):
+                np.testing.assert_array_equal(out["sum"], s)
+                np.testing.assert_array_equal(out["mean"], m)
+                assert (np.abs(out["std"] - d) <= 2 * np.spacing(d)).all(), (case["name"], w)
 
 
 def test_closed_forms():
