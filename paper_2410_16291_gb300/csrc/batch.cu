@@ -58,6 +58,7 @@ struct BatchArgs {
     int32_t nimg, nq;
     uint32_t total_tiles, total_items;
     uint32_t *ticket, *err;
+    uint32_t diag;                    // each image's tiles in anti-diagonal order
 };
 
 constexpr int kBatchWarps = 9;
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_batch(const __grid_cons
             hi = lo + a.imgs[k].ntiles;
         }
         const BImg &im = a.imgs[k];
-        const uint32_t tl = t - lo;
+        const uint32_t tl = a.diag ? diag_tile(t - lo, im.nby, im.nsx) : t - lo;
         tensormap_acquire(&im.tmS);
         tensormap_acquire(&im.tmQ);
         bool ok;
@@ -450,6 +451,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     a.total_items = item_base;
     a.ticket = reinterpret_cast<uint32_t *>(base + off_ticket);
     a.err = reinterpret_cast<uint32_t *>(base + off_err);
+    a.diag = ticket_order_diag() ? 1u : 0u;
     *out = b;
     return SWA_OK;
 }

@@ -328,8 +328,9 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
         t = __shfl_sync(kFull, t, 0);
         if ((int64_t)t >= ntiles || *(volatile uint32_t *)a.err) break;
         if (t == 0 && a.stall_tile0) continue;
-        const bool ok = DIRECT ? onepass_tile_direct<T, WQ, VEC, TH>(c, t, a.err, w)
-                               : onepass_tile<T, WQ, VEC, TH, THR>(c, t, a.err, w);
+        const uint32_t tile = a.diag ? diag_tile(t, a.nby, a.nsx) : t;
+        const bool ok = DIRECT ? onepass_tile_direct<T, WQ, VEC, TH>(c, tile, a.err, w)
+                               : onepass_tile<T, WQ, VEC, TH, THR>(c, tile, a.err, w);
         if (!ok) break;
     }
     cp_async_wait_all();
@@ -447,6 +448,7 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
     a.inc_h = a.agg_h + (size_t)p.nby * p.nsx * (2 * TH + 2);
     a.corner = reinterpret_cast<uint64_t *>(scratch + p.off_bt);
     a.stall_tile0 = (test_hooks() & SWA_HOOK_STALL_TILE0) ? 1u : 0u;
+    a.diag = ticket_order_diag() ? 1u : 0u;
     a.thr = p.thr;
     a.corner_mode = p.corner ? 1u : 0u;
     CUtensorMap tmS, tmQ;
@@ -563,6 +565,17 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
     }
     p.scratch_bytes = off;
     return p;
+}
+
+// Ticket order of the single-pass builds: anti-diagonals (diag_tile) unless
+// SWA_TICKET_ORDER=row asks for row-major order.
+bool ticket_order_diag()
+{
+    static const bool diag = [] {
+        const char *v = getenv("SWA_TICKET_ORDER");
+        return !(v && strcmp(v, "row") == 0);
+    }();
+    return diag;
 }
 
 bool corner_mode_for(int64_t nsx, int dtype)

@@ -85,6 +85,9 @@ constexpr uint32_t kCountPlan = 1u << 31;
 // records when nsx >= the dtype's threshold (SWA_CORNER_MIN_SLICES overrides
 // both built-in values, for measurements), edge mode otherwise.
 bool corner_mode_for(int64_t nsx, int dtype);
+// Ticket order of the single-pass builds: anti-diagonals unless the
+// environment variable SWA_TICKET_ORDER is "row".
+bool ticket_order_diag();
 BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype,
                     uint32_t flags, const void *image);
 swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S,
