@@ -360,8 +360,14 @@ int32_t swa_profile_end(swa_kernel_time *out, int32_t max);
  * SWA_HOOK_BAND_BUFFERS: swa_analyze_banded stages a host image in two band
  * buffers (halo rows copied on the device) even when the whole image would
  * fit, so the mode used for images larger than a quarter of the free device
- * memory can be tested on small ones. */
-enum { SWA_HOOK_STALL_TILE0 = 1u, SWA_HOOK_BAND_BUFFERS = 2u };
+ * memory can be tested on small ones.  SWA_HOOK_CORNER_MODE: single-pass
+ * builds take the corner term from the tile above-left (corner mode) instead
+ * of the horizontal records (edge mode, the default).  SWA_HOOK_ROW_ORDER:
+ * single-pass builds hand out tiles in row-major order instead of along
+ * anti-diagonals.  The last two keep the alternative paths tested; results
+ * are the same either way. */
+enum { SWA_HOOK_STALL_TILE0 = 1u, SWA_HOOK_BAND_BUFFERS = 2u, SWA_HOOK_CORNER_MODE = 4u,
+       SWA_HOOK_ROW_ORDER = 8u };
 swa_status swa_set_test_hooks(uint32_t hooks);
 
 /* ABI version: major * 10000 + minor * 100 + patch. */

@@ -22,6 +22,8 @@ SWA_OUT_SUM, SWA_OUT_MEAN, SWA_OUT_STD = 1, 2, 4
 SWA_MAX_WINDOWS = 64
 SWA_HOOK_STALL_TILE0 = 1
 SWA_HOOK_BAND_BUFFERS = 2
+SWA_HOOK_CORNER_MODE = 4
+SWA_HOOK_ROW_ORDER = 8
 
 #: C function name -> (restype, argtypes)
 _I64, _U64, _U32, _I32, _VP = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,

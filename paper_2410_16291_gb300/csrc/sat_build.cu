@@ -568,16 +568,23 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
 }
 
 // Ticket order of the single-pass builds: anti-diagonals (diag_tile) unless
-// SWA_TICKET_ORDER=row asks for row-major order.
+// SWA_TICKET_ORDER=row (or the SWA_HOOK_ROW_ORDER test hook) asks for
+// row-major order.
 bool ticket_order_diag()
 {
-    static const bool diag = [] {
+    static const bool env_row = [] {
         const char *v = getenv("SWA_TICKET_ORDER");
-        return !(v && strcmp(v, "row") == 0);
+        return v && strcmp(v, "row") == 0;
     }();
-    return diag;
+    return !env_row && !(test_hooks() & SWA_HOOK_ROW_ORDER);
 }
 
+// Corner or edge mode for an image of nsx column slices.  With diagonal
+// tickets edge mode measured at least as fast at every width (uint8 and
+// uint16, 64 to 512 slices), so it is the default; with row-major tickets
+// corner mode wins from kCornerMinSlices{U8,U16} slices.
+// SWA_CORNER_MIN_SLICES=n forces corner mode from n slices, the
+// SWA_HOOK_CORNER_MODE test hook at every width.
 bool corner_mode_for(int64_t nsx, int dtype)
 {
     static const int64_t forced = [] {
@@ -585,6 +592,8 @@ bool corner_mode_for(int64_t nsx, int dtype)
         return v && *v ? (int64_t)atoll(v) : (int64_t)0;
     }();
     if (forced > 0) return nsx >= forced;
+    if (test_hooks() & SWA_HOOK_CORNER_MODE) return true;
+    if (ticket_order_diag()) return false;
     return nsx >= (dtype == SWA_U8 ? kCornerMinSlicesU8 : kCornerMinSlicesU16);
 }
 

@@ -489,13 +489,15 @@ __device__ __forceinline__ void add_vertical(const TileCtx &a, int64_t first, in
     }
 }
 
-// Images at least this many column slices wide take the corner term K from
-// the tile above-left (corner mode); narrower ones from the horizontal
-// records (edge mode).  In a narrow image the tile above-left is only a few
-// tickets older, so chains of corner waits would run along the diagonals.
-// Measured crossover on GB300 (build throughput, both modes forced): uint8
-// from 96 slices, uint16 (half as many rows per tile, so tickets pass twice
-// as fast) from 128.  The build's host side decides and passes the mode in.
+// With row-major tickets, images at least this many column slices wide take
+// the corner term K from the tile above-left (corner mode); narrower ones
+// from the horizontal records (edge mode).  In a narrow image the tile
+// above-left is only a few tickets older, so chains of corner waits would run
+// along the diagonals.  Measured crossover on GB300 (build throughput, both
+// modes forced): uint8 from 96 slices, uint16 (half as many rows per tile, so
+// tickets pass twice as fast) from 128.  With diagonal tickets (the default)
+// edge mode wins at every width.  The build's host side decides and passes
+// the mode in.
 constexpr int64_t kCornerMinSlicesU8 = 96;
 constexpr int64_t kCornerMinSlicesU16 = 128;
 

@@ -301,7 +301,9 @@ int32_t swa_version(void) { return 10000; }
 
 swa_status swa_set_test_hooks(uint32_t hooks)
 {
-    if (hooks & ~(uint32_t)(SWA_HOOK_STALL_TILE0 | SWA_HOOK_BAND_BUFFERS)) return SWA_EINVAL;
+    if (hooks & ~(uint32_t)(SWA_HOOK_STALL_TILE0 | SWA_HOOK_BAND_BUFFERS | SWA_HOOK_CORNER_MODE |
+                            SWA_HOOK_ROW_ORDER))
+        return SWA_EINVAL;
     g_hooks.store(hooks);
     return SWA_OK;
 }

@@ -110,4 +110,6 @@ def test_test_hooks_validate(L):
     assert L.swa_set_test_hooks(0) == swa.SWA_OK
     assert L.swa_set_test_hooks(swa.SWA_HOOK_BAND_BUFFERS) == swa.SWA_OK
     assert L.swa_set_test_hooks(0) == swa.SWA_OK
-    assert L.swa_set_test_hooks(4) == swa.SWA_EINVAL
+    assert L.swa_set_test_hooks(swa.SWA_HOOK_CORNER_MODE | swa.SWA_HOOK_ROW_ORDER) == swa.SWA_OK
+    assert L.swa_set_test_hooks(0) == swa.SWA_OK
+    assert L.swa_set_test_hooks(16) == swa.SWA_EINVAL

@@ -115,18 +115,30 @@ def test_tables_row_ends_every_alignment(dtype, tail, pad, offset, twopass):
     sat.free()
 
 
-# Images at least 128 column slices (32,768 px) wide take the single pass's
-# corner mode (the corner term from the tile above-left), narrower ones the
-# edge mode; both must give the same tables.
+# The single pass takes its tiles along anti-diagonals in edge mode by
+# default; corner mode (the corner term from the tile above-left) and
+# row-major tickets are the alternatives the test hooks select.  All four
+# combinations must give the same tables.
+HOOKS = {"default": 0, "corner": swa.SWA_HOOK_CORNER_MODE, "row": swa.SWA_HOOK_ROW_ORDER,
+         "corner+row": swa.SWA_HOOK_CORNER_MODE | swa.SWA_HOOK_ROW_ORDER}
+
+
+@pytest.mark.parametrize("hook", list(HOOKS))
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 @pytest.mark.parametrize("shape,pad,offset", [((129, 32768), 0, 0), ((200, 32775), 3, 1),
-                                              ((67, 40000), 0, 0), ((5, 33000), 8, 3)])
-def test_tables_corner_mode(dtype, shape, pad, offset):
+                                              ((67, 40000), 0, 0), ((5, 33000), 8, 3),
+                                              ((1000, 1031), 0, 2), ((300, 5000), 5, 0)])
+def test_tables_lookback_modes(hook, dtype, shape, pad, offset):
     img = rand_img(*shape, dtype)
-    sat = swa.build_sat(to_device(img, pad_cols=pad, offset_px=offset), with_sq=True)
+    L = swa.lib()
+    assert L.swa_set_test_hooks(HOOKS[hook]) == 0
+    try:
+        sat = swa.build_sat(to_device(img, pad_cols=pad, offset_px=offset), with_sq=True)
+        sat.sync()
+    finally:
+        L.swa_set_test_hooks(0)
     S_ref, Q_ref = check_tables(sat, img)
     check_windows(sat, S_ref, Q_ref, [(min(33, shape[0]), 1000, 4, 7), (shape[0], shape[1], 1, 1)])
-    sat.sync()
     sat.free()
 
 
