@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="passes of the plain per-request path (workload 3)")
     ap.add_argument("--no-tune", action="store_true", help="workload 3: default batch config")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=0,
