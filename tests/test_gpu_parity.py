@@ -179,6 +179,24 @@ def test_windows_grouped_sparse_strides(dtype):
     check_windows(sat, S_ref, Q_ref, windows)
     check_windows(sat, S_ref, Q_ref, windows[:4], outputs=("sum",))
     check_windows(sat, S_ref, Q_ref, windows[6:8], outputs=("mean", "std"))
+    # Pitched outputs (row stride C + 5) for a group of four same-stride
+    # queries; the padding must stay untouched.
+    import torch
+    group = windows[:4]
+    out = []
+    for wh, ww, sy, sx in group:
+        R, C = swa.window_shape(*img.shape, wh, ww, sy, sx)
+        out.append({k: torch.full((R, C + 5), -7, dtype=torch.int64 if k == "sum"
+                                  else torch.float64, device="cuda") for k in ("sum", "mean", "std")})
+    res = sat.window_stats(group, out=[{k: v[:, :v.shape[1] - 5] for k, v in o.items()} for o in out])
+    for (wh, ww, sy, sx), got, full in zip(group, res, out):
+        want = oracle.window_sat(S_ref, Q_ref, wh, ww, sy, sx)
+        np.testing.assert_array_equal(u64(got["sum"]), want["sum"])
+        np.testing.assert_array_equal(f64(got["mean"]), want["mean"])
+        np.testing.assert_array_equal(f64(got["std"]), want["std"])
+        for k in ("sum", "mean", "std"):
+            pad = full[k][:, -5:].cpu()
+            assert (pad == -7).all(), k
     sat.free()
 
 
