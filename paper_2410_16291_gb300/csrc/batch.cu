@@ -3,14 +3,15 @@
 //
 //  1. k_batch: ONE persistent launch builds every image's tables.  Its work
 //     is a single ticket queue over the SAT tiles of all images (image after
-//     image, row-major tiles within an image), each processed by the
-//     single-pass tile routine with decoupled look-back inside its image.
+//     image; within an image along the anti-diagonals of its tile grid, or
+//     row by row), each processed by the single-pass tile routine with
+//     decoupled look-back inside its image.
 //  2. k_batch_windows: one launch evaluates every query of every image; a
 //     block covers 1024 consecutive windows of one output row of one query
 //     and finds its query by binary search over the queries' block offsets.
 //
 // The windows run in a launch of their own because the build's tiles need
-// 24 KB of shared memory per warp (8 warps per SM), while the window
+// 25 KB of shared memory per warp (9 warps per SM), while the window
 // arithmetic is ALU-bound and wants full occupancy.  A run (zeroing the
 // ticket and flags, then the two kernels) allocates nothing, so it can be
 // replayed from a CUDA graph.  Every image's tables stay in device memory

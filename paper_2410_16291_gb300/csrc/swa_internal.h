@@ -81,12 +81,14 @@ bool fits_u64(int64_t rows, int64_t cols, int dtype, bool with_q);
 // table of the indicator "pixel > thr" (staged single pass, S only; the
 // caller sets p.thr).
 constexpr uint32_t kCountPlan = 1u << 31;
-// Single-pass look-back mode for an image nsx column slices wide: corner
-// records when nsx >= the dtype's threshold (SWA_CORNER_MIN_SLICES overrides
-// both built-in values, for measurements), edge mode otherwise.
+// Single-pass look-back mode for an image nsx column slices wide: edge mode
+// with diagonal tickets; with row-major tickets corner records from the
+// dtype's threshold on.  SWA_CORNER_MIN_SLICES=n (corner mode from n slices)
+// and the SWA_HOOK_CORNER_MODE test hook override it.
 bool corner_mode_for(int64_t nsx, int dtype);
 // Ticket order of the single-pass builds: anti-diagonals unless the
-// environment variable SWA_TICKET_ORDER is "row".
+// environment variable SWA_TICKET_ORDER is "row" or the SWA_HOOK_ROW_ORDER
+// test hook is set.
 bool ticket_order_diag();
 BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype,
                     uint32_t flags, const void *image);
