@@ -38,6 +38,7 @@ METRIC = "SAT build Gpx/s + window outputs/s, % HBM peak; served p50/p99 vs plai
 # (profiles/window_stats_dense_12288x12288.md).
 INSTR_PER_WINDOW = 482.0
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e datasheet bandwidth, for context beside the measured peak
 
 
 def parse():
@@ -420,6 +421,7 @@ def run_ours(args, rank, world, local_rank):
         ach = bytes_per_launch[dom] / (avg / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "peak_kind": hbm_kind,
+                "frac_of_nominal": ach / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                 "algorithmic_bytes_per_launch": bytes_per_launch[dom],
                 "traffic": traffic_record(dom), "avg_ms": avg}
     build_ms = sum(kernels[k]["avg_ms"] * kernels[k]["launches"] for k in kernels
