@@ -79,9 +79,12 @@ struct WinArgs {
 // Windows per thread: 4 (256 apart) where the arithmetic dominates, i.e.
 // dense column strides whose corner loads mostly hit the same sectors; 1
 // where the gather dominates (column stride >= kSparseStride: neighbouring
-// threads' corners lie 32 bytes or more apart, each corner load touches its
-// own sector, and more resident warps hide more latency).
-constexpr int kSparseStride = 4;
+// threads' corners lie 24 bytes or more apart, so most corner loads touch
+// their own sector, and more resident warps hide more latency).  Measured
+// on 20,000^2 with windows 50 and 100: stride 2 runs faster dense (3.09 vs
+// 3.24 ms), stride 3 sparse (1.46 vs 1.65 ms), stride 6 sparse (0.56 vs
+// 0.70 ms).
+constexpr int kSparseStride = 3;
 inline int wins_per_thread(int64_t sx) { return sx >= kSparseStride ? 1 : 4; }
 
 // Column panel width (blocks of 256 windows) of sparse-stride groups.  With
@@ -95,8 +98,8 @@ constexpr int kPanelBlocks = 4;
 // A corner of a sparse-stride window.  The default fill brings 128 bytes
 // into L2 per miss, of which such a load uses 8; a 64-byte fill halves the
 // DRAM reads once corners lie 128 bytes or more apart (one 64-byte line per
-// corner point and table), and reads the same bytes as the 128-byte fill
-// for strides of 4 to 8.  The tables are read-only while a window kernel
+// corner point and table), and reads about the same bytes as the 128-byte
+// fill for strides of 3 to 8.  The tables are read-only while a window kernel
 // runs.
 __device__ __forceinline__ uint64_t ld_corner_sparse(const uint64_t *p)
 {
