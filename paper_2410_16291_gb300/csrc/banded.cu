@@ -429,6 +429,7 @@ swa_status swa_analyze_banded(const void *image, int64_t rows, int64_t cols, int
             x.C = C[bq.k];
             x.row0 = bq.ib * w.sy - bd.L;
             x.outputs = w.outputs;
+            x.vmax = dtype == SWA_U8 ? 255u : 65535u;
             if (host_out[bq.k]) {
                 x.out_ld = C[bq.k];
                 x.sum = static_cast<uint64_t *>(staging[(j * n + bq.k) * 3 + 0]);

@@ -338,5 +338,17 @@ SWA_HD double std_rn(uint64_t n, uint64_t sw, uint64_t qw, const Divisor &D)
     return bits_to_double(div_rn(s.sig, s.exp, D));
 }
 
+// std_rn for windows whose products n*qw and sw*sw both stay below 2^64
+// (n times the largest pixel value below 2^32): D is formed in 64 bits, the
+// roundings are std_rn's.
+SWA_HD double std_rn64(uint64_t n, uint64_t sw, uint64_t qw, const Divisor &D)
+{
+    const uint64_t d = n * qw - sw * sw;
+    if (d == 0) return 0.0;
+    const Fp r = round_u64(d);
+    const Fp s = sqrt_rn(r.sig, r.exp);
+    return bits_to_double(div_rn(s.sig, s.exp, D));
+}
+
 }  // namespace rn
 }  // namespace swa

@@ -96,6 +96,7 @@ swa_status check_window(const Handle *h, const swa_window &w, WinDesc *d)
     d->out_ld = w.out_ld;
     d->row0 = 0;
     d->outputs = o;
+    d->vmax = (h->flags & SWA_COUNT) ? 1u : h->dtype == SWA_U8 ? 255u : 65535u;
     d->sum = w.sum;
     d->mean = w.mean;
     d->std = w.std;

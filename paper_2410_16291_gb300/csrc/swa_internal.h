@@ -105,6 +105,8 @@ struct WinDesc {
     int64_t wh, ww, sy, sx, R, C, out_ld;
     int64_t row0;
     uint32_t outputs;
+    uint32_t vmax;        // largest pixel value of the table's image (255,
+                          // 65535, 1 for a count table; 0: unknown)
     uint64_t *sum;
     double *mean, *std;
 };

@@ -115,11 +115,16 @@ __device__ __forceinline__ uint64_t ld_corner(const uint64_t *p)
     else return __ldg(p);
 }
 
+// Rounding paths of mean and std: FP64 division and square root (window
+// areas of 2^32 or more), the integer path on a 128-bit D, the integer path
+// on a 64-bit D.
+constexpr int kRnFp64 = 0, kRnInt128 = 1, kRnInt64 = 2;
+
 // The WPT windows (i, jb), (i, jb + 256), ... of one query: all corner loads
 // first (independent, so they are in flight together), then the arithmetic.
 // With TL, the top-left corner's S and Q entries are given (tl_s, tl_q:
 // WPT == 1, loaded once for all queries of a group).
-template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN, int WPT, bool TL = false>
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, int RN, int WPT, bool TL = false>
 __device__ __forceinline__ void window_row(const WinArgs &a, const WinQ &q, int64_t i, int64_t jb,
                                            uint64_t tl_s = 0, uint64_t tl_q = 0)
 {
@@ -161,9 +166,11 @@ __device__ __forceinline__ void window_row(const WinArgs &a, const WinQ &q, int6
         if (DO_SUM) q.w.sum[o] = sw[m];
         if (DO_MEAN)
             q.w.mean[o] =
-                INT_RN ? rn::mean_rn(sw[m], q.div) : __ddiv_rn(__ull2double_rn(sw[m]), q.n_d);
+                RN != kRnFp64 ? rn::mean_rn(sw[m], q.div) : __ddiv_rn(__ull2double_rn(sw[m]), q.n_d);
         if (DO_STD) {
-            if (INT_RN) {
+            if (RN == kRnInt64) {
+                q.w.std[o] = rn::std_rn64(q.n, sw[m], qw[m], q.div);
+            } else if (RN == kRnInt128) {
                 q.w.std[o] = rn::std_rn(q.n, sw[m], qw[m], q.div);
             } else {
                 const unsigned __int128 D =
@@ -188,7 +195,7 @@ __device__ __forceinline__ const WinGroup &group_of(const WinArgs &a, uint32_t b
 // Dense column strides: every group holds one query; a block covers 1,024
 // consecutive windows of one output row (thread t: windows t, t + 256,
 // t + 512, t + 768, so every load and store instruction stays coalesced).
-template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN>
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, int RN>
 __global__ void __launch_bounds__(256) k_windows_dense(const __grid_constant__ WinArgs a)
 {
     const uint32_t bid = blockIdx.x;
@@ -197,13 +204,13 @@ __global__ void __launch_bounds__(256) k_windows_dense(const __grid_constant__ W
     const uint32_t nbx = (uint32_t)G.nbx;
     const uint32_t i = blk / nbx;
     const int64_t jb = (int64_t)(blk - i * nbx) * (256 * 4) + threadIdx.x;
-    window_row<DO_SUM, DO_MEAN, DO_STD, INT_RN, 4>(a, a.q[G.q0], i, jb);
+    window_row<DO_SUM, DO_MEAN, DO_STD, RN, 4>(a, a.q[G.q0], i, jb);
 }
 
 // Sparse column strides: a block covers 256 consecutive positions of one
 // union-grid row of a group and evaluates each of the group's queries there
 // (one window per thread and query).
-template <bool DO_SUM, bool DO_MEAN, bool DO_STD, bool INT_RN>
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, int RN>
 __global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ WinArgs a)
 {
     const uint32_t bid = blockIdx.x;
@@ -247,27 +254,27 @@ __global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ 
         for (int k = G.q0; k < G.q0 + G.nq; ++k) {
             const WinQ &q = a.q[k];
             if ((int64_t)i >= q.w.R) continue;         // uniform over the block
-            window_row<DO_SUM, DO_MEAN, DO_STD, INT_RN, 1, true>(a, q, i, jb, tl_s, tl_q);
+            window_row<DO_SUM, DO_MEAN, DO_STD, RN, 1, true>(a, q, i, jb, tl_s, tl_q);
         }
     } else {
 #pragma unroll 1
         for (int k = G.q0; k < G.q0 + G.nq; ++k) {
             const WinQ &q = a.q[k];
             if ((int64_t)i >= q.w.R) continue;         // uniform over the block
-            window_row<DO_SUM, DO_MEAN, DO_STD, INT_RN, 1>(a, q, i, jb);
+            window_row<DO_SUM, DO_MEAN, DO_STD, RN, 1>(a, q, i, jb);
         }
     }
 }
 
-template <bool A, bool B, bool C, bool I>
+template <bool A, bool B, bool C, int RN>
 void launch_one(const WinArgs &a, unsigned blocks, int wpt, cudaStream_t s)
 {
     LaunchScope ls("window_stats", s);
-    if (wpt == 1) k_windows_sparse<A, B, C, I><<<blocks, 256, 0, s>>>(a);
-    else k_windows_dense<A, B, C, I><<<blocks, 256, 0, s>>>(a);
+    if (wpt == 1) k_windows_sparse<A, B, C, RN><<<blocks, 256, 0, s>>>(a);
+    else k_windows_dense<A, B, C, RN><<<blocks, 256, 0, s>>>(a);
 }
 
-swa_status flush(WinArgs &a, int64_t blocks, uint32_t o, bool int_rn, int wpt, cudaStream_t s)
+swa_status flush(WinArgs &a, int64_t blocks, uint32_t o, int mode, int wpt, cudaStream_t s)
 {
     if (a.ng == 0 || blocks == 0) return SWA_OK;
     if (blocks > 0x7fffffffLL) {
@@ -276,16 +283,23 @@ swa_status flush(WinArgs &a, int64_t blocks, uint32_t o, bool int_rn, int wpt, c
     }
     const bool ds = o & SWA_OUT_SUM, dm = o & SWA_OUT_MEAN, dd = o & SWA_OUT_STD;
     const unsigned nb = (unsigned)blocks;
-#define SWA_L(A, B, C)                                                   \
-    (int_rn ? launch_one<A, B, C, true>(a, nb, wpt, s) : launch_one<A, B, C, false>(a, nb, wpt, s))
+#define SWA_L(A, B, C)                                                              \
+    (mode == kRnFp64     ? launch_one<A, B, C, kRnFp64>(a, nb, wpt, s)                   \
+     : mode == kRnInt128 ? launch_one<A, B, C, kRnInt128>(a, nb, wpt, s)                 \
+                       : launch_one<A, B, C, kRnInt64>(a, nb, wpt, s))
+// Without std the 64-bit variant is never asked for (mode_of folds it).
+#define SWA_L2(A, B, C)                                                             \
+    (mode == kRnFp64 ? launch_one<A, B, C, kRnFp64>(a, nb, wpt, s)                      \
+                   : launch_one<A, B, C, kRnInt128>(a, nb, wpt, s))
     if (ds && dm && dd) SWA_L(true, true, true);
-    else if (ds && dm) SWA_L(true, true, false);
+    else if (ds && dm) SWA_L2(true, true, false);
     else if (ds && dd) SWA_L(true, false, true);
     else if (dm && dd) SWA_L(false, true, true);
-    else if (ds) SWA_L(true, false, false);
-    else if (dm) SWA_L(false, true, false);
+    else if (ds) SWA_L2(true, false, false);
+    else if (dm) SWA_L2(false, true, false);
     else if (dd) SWA_L(false, false, true);
 #undef SWA_L
+#undef SWA_L2
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("window launch failed: %s", cudaGetErrorString(e));
@@ -305,14 +319,23 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
                           int n, cudaStream_t s)
 {
     bool done[SWA_MAX_WINDOWS] = {false};
-    auto int_rn_of = [&](int k) { return (uint64_t)(w[k].wh * w[k].ww) < (1ull << 32); };
+    // Rounding path of query k: the integer one for areas below 2^32, with
+    // D in 64 bits when n times the largest pixel value stays below 2^32
+    // (and std is asked for); FP64 for larger areas.
+    auto mode_of = [&](int k) {
+        const uint64_t area = (uint64_t)(w[k].wh * w[k].ww);
+        if (area >= (1ull << 32)) return kRnFp64;
+        const bool d64 = (w[k].outputs & SWA_OUT_STD) && w[k].vmax &&
+                         area * (uint64_t)w[k].vmax < (1ull << 32);
+        return d64 ? kRnInt64 : kRnInt128;
+    };
     for (int k0 = 0; k0 < n; ++k0) {
         if (done[k0]) continue;
         const uint32_t o = w[k0].outputs;
-        const bool int_rn = int_rn_of(k0);
+        const int mode = mode_of(k0);
         const int wpt = wins_per_thread(w[k0].sx);
         auto fits = [&](int k) {
-            return !done[k] && w[k].outputs == o && int_rn_of(k) == int_rn &&
+            return !done[k] && w[k].outputs == o && mode_of(k) == mode &&
                    wins_per_thread(w[k].sx) == wpt;
         };
         WinArgs a;
@@ -340,7 +363,7 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
             }
             if (m == 0) continue;
             if (a.nq + m > kQPerLaunch || a.ng == kQPerLaunch) {
-                swa_status st = flush(a, blocks, o, int_rn, wpt, s);
+                swa_status st = flush(a, blocks, o, mode, wpt, s);
                 if (st != SWA_OK) return st;
                 a.nq = 0;
                 a.ng = 0;
@@ -365,10 +388,10 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
                 q.w = w[k];
                 q.n = area;
                 q.n_d = (double)area;
-                q.div = rn::make_divisor(int_rn ? (uint32_t)area : 1u);
+                q.div = rn::make_divisor(mode != kRnFp64 ? (uint32_t)area : 1u);
             }
         }
-        swa_status st = flush(a, blocks, o, int_rn, wpt, s);
+        swa_status st = flush(a, blocks, o, mode, wpt, s);
         if (st != SWA_OK) return st;
     }
     return SWA_OK;

@@ -14,6 +14,16 @@ void rn_stats_bulk(const uint64_t *n, const uint64_t *sw, const uint64_t *qw, in
     }
 }
 
+// std through the 64-bit-D variant (valid when n * max pixel < 2^32).
+void rn_std64_bulk(const uint64_t *n, const uint64_t *sw, const uint64_t *qw, int64_t count,
+                   double *stdv)
+{
+    for (int64_t i = 0; i < count; ++i) {
+        const swa::rn::Divisor D = swa::rn::make_divisor((uint32_t)n[i]);
+        stdv[i] = swa::rn::std_rn64(n[i], sw[i], qw[i], D);
+    }
+}
+
 double rn_u128(uint64_t hi, uint64_t lo)
 {
     const swa::rn::Fp f = swa::rn::round_u128(hi, lo);

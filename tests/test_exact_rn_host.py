@@ -25,6 +25,7 @@ def rn():
     L = ctypes.CDLL(out)
     vp = ctypes.c_void_p
     L.rn_stats_bulk.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp]
+    L.rn_std64_bulk.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
     L.rn_u128.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
     L.rn_u128.restype = ctypes.c_double
     L.rn_sqrt.argtypes = [ctypes.c_double]
@@ -121,3 +122,23 @@ def test_division_by_powers_of_two_is_exact(rn):
         for _ in range(300):
             a = int(rng.integers(0, 2**63)) >> int(rng.integers(0, 63))
             assert rn.rn_div(a, n) == float(a) / float(n), (a, n)
+
+
+@pytest.mark.parametrize("vmax", [1, 255, 65535])
+def test_std_64bit_variant_equals_128bit_path(rn, vmax):
+    """std_rn64 (D formed in 64 bits, used when n * vmax < 2^32) gives the
+    same bits as std_rn and the oracle for windows up to that bound,
+    including the largest n it is used for."""
+    rng = np.random.default_rng(vmax)
+    nmax = (2 ** 32 - 1) // vmax
+    n, sw, qw = moments(rng, 20000, nmax, vmax)
+    n[:3] = nmax
+    sw[:3] = [0, nmax * vmax, nmax * vmax // 2]
+    qw[:3] = [0, nmax * vmax * vmax, (nmax * vmax // 2) * vmax]
+    s64 = np.empty(len(n))
+    rn.rn_std64_bulk(np.ascontiguousarray(n).ctypes.data, np.ascontiguousarray(sw).ctypes.data,
+                     np.ascontiguousarray(qw).ctypes.data, len(n), s64.ctypes.data)
+    _, s128 = run_bulk(rn, n, sw, qw)
+    np.testing.assert_array_equal(s64, s128)
+    _, want = oracle.stats_bulk(n, sw, qw)
+    np.testing.assert_array_equal(s64, want)
