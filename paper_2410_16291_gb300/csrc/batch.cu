@@ -49,6 +49,7 @@ struct BQuery {
     double n_d;
     rn::Divisor div;
     int32_t img, int_rn;
+    int32_t d64;                      // std from a 64-bit D (n * max pixel < 2^32)
     int64_t nbx;                      // blocks per output row
     uint32_t item_base, nitems;       // first block, blocks
 };
@@ -158,7 +159,8 @@ __global__ void __launch_bounds__(256) k_batch_windows(const BQuery *__restrict_
             if (left) qw -= __ldg(Qb + x0 - 1);
             if (top && left) qw += __ldg(Qt + x0 - 1);
             if (q.int_rn) {
-                q.w.std[oi] = rn::std_rn(q.n, sw, qw, q.div);
+                q.w.std[oi] = q.d64 ? rn::std_rn64(q.n, sw, qw, q.div)
+                                    : rn::std_rn(q.n, sw, qw, q.div);
             } else {
                 const unsigned __int128 D =
                     (unsigned __int128)q.n * qw - (unsigned __int128)sw * sw;
@@ -420,6 +422,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
             q.n = (uint64_t)(w.wh * w.ww);
             q.n_d = (double)q.n;
             q.int_rn = q.n < (1ull << 32);
+            q.d64 = q.int_rn && q.n * (it.dtype == SWA_U8 ? 255ull : 65535ull) < (1ull << 32);
             q.div = rn::make_divisor(q.int_rn ? (uint32_t)q.n : 1u);
             q.img = pos;
             q.nbx = (q.w.C + kBWinPerBlock - 1) / kBWinPerBlock;
