@@ -191,11 +191,14 @@ def traffic_record(kernel):
     e = d.get(kernel)
     if not e:
         return None
-    src = os.path.join(ROOT, "paper_2410_16291_gb300", "csrc", e["source"])
-    if not os.path.exists(src):
-        return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if h != e["source_sha"]:
+    names = e["source"] if isinstance(e["source"], list) else [e["source"]]
+    h = hashlib.sha256()
+    for name in names:                       # the kernel's sources, in order
+        src = os.path.join(ROOT, "paper_2410_16291_gb300", "csrc", name)
+        if not os.path.exists(src):
+            return None
+        h.update(open(src, "rb").read())
+    if h.hexdigest()[:16] != e["source_sha"]:
         return None
     return e["bytes_per_launch_full"]
 
