@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--threshold", type=int, default=None,
                     help="build the count table of pixels > THRESHOLD instead of S and Q "
                          "(windows then give count / fraction / indicator std)")
+    ap.add_argument("--batch-images", type=int, default=0,
+                    help="workload 3: use only the first N images (0: all 256)")
     ap.add_argument("--windows", default="",
                     help="custom windows w/stride list, e.g. 100/1,256/16")
     return ap.parse_args()
@@ -500,6 +502,8 @@ def run_batch(args, rank, world, local_rank):
     if dist:
         import torch.distributed as td
     imgs = synth.workload(3)
+    if args.batch_images:
+        imgs = imgs[:args.batch_images]          # a smaller batch (profiling)
     t0 = time.perf_counter()
     devs, wins = [], []
     for im in imgs:
