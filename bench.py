@@ -181,9 +181,10 @@ def distinct_corner_bytes(rows, cols, wh, ww, sy, sx, tables):
     return int((ry >= 0).sum()) * int((cx >= 0).sum()) * 8 * tables
 
 
-def traffic_record(kernel):
-    """ncu DRAM bytes per launch for `kernel`, if the committed capture is of
-    the current source; else None."""
+def traffic_record(kernel, case=None):
+    """ncu DRAM bytes per launch for `kernel` on the workload `case` (e.g.
+    "70000x85000 u8 S+Q"), if the committed capture is of the current source
+    and was scaled to that case; else None."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
@@ -191,7 +192,13 @@ def traffic_record(kernel):
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel)
-    if not e:
+    if not e or e.get("full_case") != case:
+        return None
+    # The capture is of the default build; variants selected by environment
+    # variables (look-back mode, ticket order, the direct variant) move
+    # other bytes.
+    if any(os.environ.get(v) for v in ("SWA_SAT_VARIANT", "SWA_TICKET_ORDER",
+                                        "SWA_CORNER_MIN_SLICES")):
         return None
     names = e["source"] if isinstance(e["source"], list) else [e["source"]]
     h = hashlib.sha256()
@@ -428,7 +435,10 @@ def run_ours(args, rank, world, local_rank):
                 "frac": ach / hbm, "peak_kind": hbm_kind,
                 "frac_of_nominal": ach / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                 "algorithmic_bytes_per_launch": bytes_per_launch[dom],
-                "traffic": traffic_record(dom), "avg_ms": avg}
+                "traffic": traffic_record(dom, "%dx%d %s %s" % (
+                    im.rows, im.cols, im.dtype,
+                    "count" if args.threshold is not None else
+                    ("two-pass S+Q" if args.twopass else "S+Q"))), "avg_ms": avg}
     build_ms = sum(kernels[k]["avg_ms"] * kernels[k]["launches"] for k in kernels
                    if k.startswith("sat_")) / args.steps
     win_ms = sum(kernels[k]["avg_ms"] * kernels[k]["launches"] for k in kernels
