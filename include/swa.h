@@ -104,6 +104,11 @@ typedef struct {
  * with SWA_WITH_SQ) is >= 2^64, so that no entry can wrap: for uint8 this
  * never happens below 2.8e14 px; a uint16 image with Q must have fewer than
  * 4,295,098,372 px.
+ * Environment variables read once per process select build variants kept
+ * for measurements (the tables are the same): SWA_TICKET_ORDER=row (tiles in
+ * row-major order instead of along anti-diagonals), SWA_CORNER_MIN_SLICES=n
+ * (corner-record look-back for images of n or more 256-column slices),
+ * SWA_SAT_VARIANT=direct (no shared-memory staging of the image tile).
  */
 swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols,
                          int64_t pitch_bytes, swa_dtype dtype, uint32_t flags,
