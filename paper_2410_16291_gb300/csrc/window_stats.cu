@@ -46,6 +46,9 @@ struct WinQ {
     uint64_t n;           // window area
     double n_d;
     rn::Divisor div;      // n as an invariant divisor (integer path)
+    int32_t kw;           // ww / sx when that is a whole number below 32, else 0:
+                          // a window's right corners are the left corners
+                          // of the window kw positions further along the row
 };
 
 // Queries of a launch evaluated together: every thread computes, for each
@@ -119,6 +122,7 @@ __device__ __forceinline__ uint64_t ld_corner(const uint64_t *p)
 // areas of 2^32 or more), the integer path on a 128-bit D, the integer path
 // on a 64-bit D.
 constexpr int kRnFp64 = 0, kRnInt128 = 1, kRnInt64 = 2;
+constexpr unsigned kFullMask = 0xffffffffu;
 
 // The WPT windows (i, jb), (i, jb + 256), ... of one query: all corner loads
 // first (independent, so they are in flight together), then the arithmetic.
@@ -192,6 +196,64 @@ __device__ __forceinline__ const WinGroup &group_of(const WinArgs &a, uint32_t b
     return a.g[g];
 }
 
+// One window per lane of a sparse-stride query with kw > 0 in a group that
+// shares the top-left corner: the lane loads its bottom-left corner, and
+// takes both right corners from lane + kw (its left corners are this
+// window's right ones) where that lane is in the warp, loading them itself
+// otherwise.  Left corners are loaded wherever they lie inside the table
+// row, so every lane that serves as a partner has them.
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, int RN>
+__device__ __forceinline__ void window_lanes(const WinArgs &a, const WinQ &q, int64_t i,
+                                             int64_t jb, uint64_t tl_s, uint64_t tl_q)
+{
+    const int lane = threadIdx.x & 31, kw = q.kw;
+    const int64_t y0 = q.w.row0 + i * q.w.sy, y1 = y0 + q.w.wh - 1;
+    const int64_t ld = a.ld;
+    const bool top = y0 > 0;
+    const int64_t x0 = jb * q.w.sx, x1 = x0 + q.w.ww - 1;
+    const bool valid = jb < q.w.C;
+    const uint64_t *Sb = a.S + y1 * ld, *Qb = a.Q + y1 * ld;
+    uint64_t bl_s = 0, bl_q = 0;
+    if (x0 > 0 && x0 - 1 < ld) {
+        bl_s = ld_corner_sparse(Sb + x0 - 1);
+        if (DO_STD) bl_q = ld_corner_sparse(Qb + x0 - 1);
+    }
+    uint64_t tr_s = __shfl_down_sync(kFullMask, tl_s, kw);
+    uint64_t br_s = __shfl_down_sync(kFullMask, bl_s, kw);
+    uint64_t tr_q = 0, br_q = 0;
+    if (DO_STD) {
+        tr_q = __shfl_down_sync(kFullMask, tl_q, kw);
+        br_q = __shfl_down_sync(kFullMask, bl_q, kw);
+    }
+    if (!valid) return;
+    if (lane + kw >= 32) {                             // partner outside the warp
+        const uint64_t *St = a.S + (y0 - 1) * ld, *Qt = a.Q + (y0 - 1) * ld;
+        br_s = ld_corner_sparse(Sb + x1);
+        tr_s = top ? ld_corner_sparse(St + x1) : 0;
+        if (DO_STD) {
+            br_q = ld_corner_sparse(Qb + x1);
+            tr_q = top ? ld_corner_sparse(Qt + x1) : 0;
+        }
+    }
+    const uint64_t sw = br_s - tr_s - bl_s + tl_s;
+    const uint64_t qw = DO_STD ? br_q - tr_q - bl_q + tl_q : 0;
+    const int64_t o = i * q.w.out_ld + jb;
+    if (DO_SUM) q.w.sum[o] = sw;
+    if (DO_MEAN)
+        q.w.mean[o] = RN != kRnFp64 ? rn::mean_rn(sw, q.div) : __ddiv_rn(__ull2double_rn(sw), q.n_d);
+    if (DO_STD) {
+        if (RN == kRnInt64) {
+            q.w.std[o] = rn::std_rn64(q.n, sw, qw, q.div);
+        } else if (RN == kRnInt128) {
+            q.w.std[o] = rn::std_rn(q.n, sw, qw, q.div);
+        } else {
+            const unsigned __int128 D = (unsigned __int128)q.n * qw - (unsigned __int128)sw * sw;
+            const double d = u128_to_double_rn((uint64_t)(D >> 64), (uint64_t)D);
+            q.w.std[o] = __ddiv_rn(__dsqrt_rn(d), q.n_d);
+        }
+    }
+}
+
 // Dense column strides: every group holds one query; a block covers 1,024
 // consecutive windows of one output row (thread t: windows t, t + 256,
 // t + 512, t + 768, so every load and store instruction stays coalesced).
@@ -245,7 +307,7 @@ __global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ 
         const WinQ &q0 = a.q[G.q0];
         const int64_t y0 = q0.w.row0 + (int64_t)i * q0.w.sy, x0 = jb * q0.w.sx;
         uint64_t tl_s = 0, tl_q = 0;
-        if (y0 > 0 && x0 > 0 && jb < G.C) {
+        if (y0 > 0 && x0 > 0 && x0 - 1 < a.ld) {       // inside the table row
             const int64_t off = (y0 - 1) * a.ld + x0 - 1;
             tl_s = ld_corner_sparse(a.S + off);
             if (DO_STD) tl_q = ld_corner_sparse(a.Q + off);
@@ -254,7 +316,10 @@ __global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ 
         for (int k = G.q0; k < G.q0 + G.nq; ++k) {
             const WinQ &q = a.q[k];
             if ((int64_t)i >= q.w.R) continue;         // uniform over the block
-            window_row<DO_SUM, DO_MEAN, DO_STD, RN, 1, true>(a, q, i, jb, tl_s, tl_q);
+            if (q.kw)                                  // uniform over the block
+                window_lanes<DO_SUM, DO_MEAN, DO_STD, RN>(a, q, i, jb, tl_s, tl_q);
+            else
+                window_row<DO_SUM, DO_MEAN, DO_STD, RN, 1, true>(a, q, i, jb, tl_s, tl_q);
         }
     } else {
 #pragma unroll 1
@@ -389,6 +454,8 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
                 q.n = area;
                 q.n_d = (double)area;
                 q.div = rn::make_divisor(mode != kRnFp64 ? (uint32_t)area : 1u);
+                q.kw = (wpt == 1 && w[k].ww % w[k].sx == 0 && w[k].ww / w[k].sx < 32)
+                           ? (int32_t)(w[k].ww / w[k].sx) : 0;
             }
         }
         swa_status st = flush(a, blocks, o, mode, wpt, s);
