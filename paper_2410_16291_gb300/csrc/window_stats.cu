@@ -46,9 +46,9 @@ struct WinQ {
     uint64_t n;           // window area
     double n_d;
     rn::Divisor div;      // n as an invariant divisor (integer path)
-    int32_t kw;           // ww / sx when that is a whole number below 32, else 0:
-                          // a window's right corners are the left corners
-                          // of the window kw positions further along the row
+    int32_t kw;           // ww / sx when that is a whole number below 256,
+                          // else 0: a window's right corners are the left
+                          // corners of the window kw positions further along
 };
 
 // Queries of a launch evaluated together: every thread computes, for each
@@ -122,7 +122,6 @@ __device__ __forceinline__ uint64_t ld_corner(const uint64_t *p)
 // areas of 2^32 or more), the integer path on a 128-bit D, the integer path
 // on a 64-bit D.
 constexpr int kRnFp64 = 0, kRnInt128 = 1, kRnInt64 = 2;
-constexpr unsigned kFullMask = 0xffffffffu;
 
 // The WPT windows (i, jb), (i, jb + 256), ... of one query: all corner loads
 // first (independent, so they are in flight together), then the arithmetic.
@@ -196,45 +195,57 @@ __device__ __forceinline__ const WinGroup &group_of(const WinArgs &a, uint32_t b
     return a.g[g];
 }
 
-// One window per lane of a sparse-stride query with kw > 0 in a group that
-// shares the top-left corner: the lane loads its bottom-left corner, and
-// takes both right corners from lane + kw (its left corners are this
-// window's right ones) where that lane is in the warp, loading them itself
-// otherwise.  Left corners are loaded wherever they lie inside the table
-// row, so every lane that serves as a partner has them.
+// One window per thread of a sparse-stride query with kw > 0 in a group
+// that shares the top-left corner.  The block's 256 threads hold 256
+// consecutive grid positions; a window's right corners are the left corners
+// of the position kw further along, so every thread publishes its left
+// corners in shared memory (the top-left one once per block, the bottom-left
+// one per query) and takes its right corners from thread + kw, loading them
+// itself only where that thread lies past the block.  Left corners are
+// loaded wherever they lie inside the table row, so every thread that serves
+// as a partner has them.  Called by every thread of the block (barriers).
 template <bool DO_SUM, bool DO_MEAN, bool DO_STD, int RN>
-__device__ __forceinline__ void window_lanes(const WinArgs &a, const WinQ &q, int64_t i,
-                                             int64_t jb, uint64_t tl_s, uint64_t tl_q)
+__device__ __forceinline__ void window_shared(const WinArgs &a, const WinQ &q, int64_t i,
+                                              int64_t jb, const uint64_t *sh_tl,
+                                              uint64_t *sh_bl)
 {
-    const int lane = threadIdx.x & 31, kw = q.kw;
+    const int t = threadIdx.x, p = t + q.kw;
     const int64_t y0 = q.w.row0 + i * q.w.sy, y1 = y0 + q.w.wh - 1;
     const int64_t ld = a.ld;
     const bool top = y0 > 0;
     const int64_t x0 = jb * q.w.sx, x1 = x0 + q.w.ww - 1;
-    const bool valid = jb < q.w.C;
     const uint64_t *Sb = a.S + y1 * ld, *Qb = a.Q + y1 * ld;
     uint64_t bl_s = 0, bl_q = 0;
     if (x0 > 0 && x0 - 1 < ld) {
         bl_s = ld_corner_sparse(Sb + x0 - 1);
         if (DO_STD) bl_q = ld_corner_sparse(Qb + x0 - 1);
     }
-    uint64_t tr_s = __shfl_down_sync(kFullMask, tl_s, kw);
-    uint64_t br_s = __shfl_down_sync(kFullMask, bl_s, kw);
-    uint64_t tr_q = 0, br_q = 0;
-    if (DO_STD) {
-        tr_q = __shfl_down_sync(kFullMask, tl_q, kw);
-        br_q = __shfl_down_sync(kFullMask, bl_q, kw);
-    }
-    if (!valid) return;
-    if (lane + kw >= 32) {                             // partner outside the warp
-        const uint64_t *St = a.S + (y0 - 1) * ld, *Qt = a.Q + (y0 - 1) * ld;
-        br_s = ld_corner_sparse(Sb + x1);
-        tr_s = top ? ld_corner_sparse(St + x1) : 0;
-        if (DO_STD) {
-            br_q = ld_corner_sparse(Qb + x1);
-            tr_q = top ? ld_corner_sparse(Qt + x1) : 0;
+    sh_bl[t] = bl_s;
+    if (DO_STD) sh_bl[256 + t] = bl_q;
+    __syncthreads();
+    const bool valid = jb < q.w.C;
+    uint64_t tr_s = 0, tr_q = 0, br_s = 0, br_q = 0;
+    if (valid) {
+        if (p < 256) {
+            tr_s = sh_tl[p];
+            br_s = sh_bl[p];
+            if (DO_STD) {
+                tr_q = sh_tl[256 + p];
+                br_q = sh_bl[256 + p];
+            }
+        } else {                                       // partner past the block
+            const uint64_t *St = a.S + (y0 - 1) * ld, *Qt = a.Q + (y0 - 1) * ld;
+            br_s = ld_corner_sparse(Sb + x1);
+            tr_s = top ? ld_corner_sparse(St + x1) : 0;
+            if (DO_STD) {
+                br_q = ld_corner_sparse(Qb + x1);
+                tr_q = top ? ld_corner_sparse(Qt + x1) : 0;
+            }
         }
     }
+    __syncthreads();                                   // sh_bl is reused by the next query
+    if (!valid) return;
+    const uint64_t tl_s = sh_tl[t], tl_q = DO_STD ? sh_tl[256 + t] : 0;
     const uint64_t sw = br_s - tr_s - bl_s + tl_s;
     const uint64_t qw = DO_STD ? br_q - tr_q - bl_q + tl_q : 0;
     const int64_t o = i * q.w.out_ld + jb;
@@ -312,12 +323,16 @@ __global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ 
             tl_s = ld_corner_sparse(a.S + off);
             if (DO_STD) tl_q = ld_corner_sparse(a.Q + off);
         }
+        __shared__ uint64_t sh_tl[2 * 256], sh_bl[2 * 256];   // S, then Q
+        sh_tl[threadIdx.x] = tl_s;
+        if (DO_STD) sh_tl[256 + threadIdx.x] = tl_q;
+        __syncthreads();
 #pragma unroll 1
         for (int k = G.q0; k < G.q0 + G.nq; ++k) {
             const WinQ &q = a.q[k];
             if ((int64_t)i >= q.w.R) continue;         // uniform over the block
             if (q.kw)                                  // uniform over the block
-                window_lanes<DO_SUM, DO_MEAN, DO_STD, RN>(a, q, i, jb, tl_s, tl_q);
+                window_shared<DO_SUM, DO_MEAN, DO_STD, RN>(a, q, i, jb, sh_tl, sh_bl);
             else
                 window_row<DO_SUM, DO_MEAN, DO_STD, RN, 1, true>(a, q, i, jb, tl_s, tl_q);
         }
@@ -454,7 +469,7 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
                 q.n = area;
                 q.n_d = (double)area;
                 q.div = rn::make_divisor(mode != kRnFp64 ? (uint32_t)area : 1u);
-                q.kw = (wpt == 1 && w[k].ww % w[k].sx == 0 && w[k].ww / w[k].sx < 32)
+                q.kw = (wpt == 1 && w[k].ww % w[k].sx == 0 && w[k].ww / w[k].sx < 256)
                            ? (int32_t)(w[k].ww / w[k].sx) : 0;
             }
         }
