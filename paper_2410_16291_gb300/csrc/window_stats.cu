@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(256) k_windows_dense(const __grid_constant__ W
 // union-grid row of a group and evaluates each of the group's queries there
 // (one window per thread and query).
 template <bool DO_SUM, bool DO_MEAN, bool DO_STD, int RN>
-__global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ WinArgs a)
+__global__ void __launch_bounds__(256, 8) k_windows_sparse(const __grid_constant__ WinArgs a)
 {
     const uint32_t bid = blockIdx.x;
     const WinGroup &G = group_of(a, bid);
@@ -311,6 +311,7 @@ __global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ 
         }
     }
     const int64_t jb = (int64_t)bx * 256 + threadIdx.x;
+    __shared__ uint64_t sh_tl[2 * 256], sh_bl[2 * 256];   // corners: S, then Q
     if (G.share_tl) {
         // One load of the shared top-left corner (zero on the table's first
         // row or column) for all queries: 7 of 8 corner loads per window
@@ -323,7 +324,6 @@ __global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ 
             tl_s = ld_corner_sparse(a.S + off);
             if (DO_STD) tl_q = ld_corner_sparse(a.Q + off);
         }
-        __shared__ uint64_t sh_tl[2 * 256], sh_bl[2 * 256];   // S, then Q
         sh_tl[threadIdx.x] = tl_s;
         if (DO_STD) sh_tl[256 + threadIdx.x] = tl_q;
         __syncthreads();
@@ -337,11 +337,28 @@ __global__ void __launch_bounds__(256) k_windows_sparse(const __grid_constant__ 
                 window_row<DO_SUM, DO_MEAN, DO_STD, RN, 1, true>(a, q, i, jb, tl_s, tl_q);
         }
     } else {
+        // Queries with their own top-left corner (a single query of its
+        // strides, or banded queries starting at different table rows): a
+        // query with kw > 0 publishes its own top-left corners first.
 #pragma unroll 1
         for (int k = G.q0; k < G.q0 + G.nq; ++k) {
             const WinQ &q = a.q[k];
             if ((int64_t)i >= q.w.R) continue;         // uniform over the block
-            window_row<DO_SUM, DO_MEAN, DO_STD, RN, 1>(a, q, i, jb);
+            if (q.kw) {                                // uniform over the block
+                const int64_t y0 = q.w.row0 + (int64_t)i * q.w.sy, x0 = jb * q.w.sx;
+                uint64_t tl_s = 0, tl_q = 0;
+                if (y0 > 0 && x0 > 0 && x0 - 1 < a.ld) {
+                    const int64_t off = (y0 - 1) * a.ld + x0 - 1;
+                    tl_s = ld_corner_sparse(a.S + off);
+                    if (DO_STD) tl_q = ld_corner_sparse(a.Q + off);
+                }
+                sh_tl[threadIdx.x] = tl_s;             // own slot: read back by this
+                if (DO_STD) sh_tl[256 + threadIdx.x] = tl_q;   // thread after the barriers
+                __syncthreads();
+                window_shared<DO_SUM, DO_MEAN, DO_STD, RN>(a, q, i, jb, sh_tl, sh_bl);
+            } else {
+                window_row<DO_SUM, DO_MEAN, DO_STD, RN, 1>(a, q, i, jb);
+            }
         }
     }
 }

@@ -176,6 +176,10 @@ def test_windows_grouped_sparse_strides(dtype):
                (613, 9000, 4, 4), (1, 1, 4, 4), (33, 33, 16, 5), (256, 512, 16, 5),
                (5, 17, 1, 4), (12, 12, 1, 1)]
     windows += [(3 + 5 * k, 2 + 7 * k, 5, 7) for k in range(21)]
+    # single queries of their strides whose width is a multiple of the
+    # stride (right corners exchanged through shared memory without a
+    # shared top-left load)
+    windows += [(30, 30, 5, 5), (7, 21, 3, 3), (613, 600, 6, 6)]
     check_windows(sat, S_ref, Q_ref, windows)
     check_windows(sat, S_ref, Q_ref, windows[:4], outputs=("sum",))
     check_windows(sat, S_ref, Q_ref, windows[6:8], outputs=("mean", "std"))
