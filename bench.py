@@ -194,12 +194,6 @@ def traffic_record(kernel, case=None):
     e = d.get(kernel)
     if not e or e.get("full_case") != case:
         return None
-    # The capture is of the default build; variants selected by environment
-    # variables (look-back mode, ticket order, the direct variant) move
-    # other bytes.
-    if any(os.environ.get(v) for v in ("SWA_SAT_VARIANT", "SWA_TICKET_ORDER",
-                                        "SWA_CORNER_MIN_SLICES")):
-        return None
     names = e["source"] if isinstance(e["source"], list) else [e["source"]]
     h = hashlib.sha256()
     for name in names:                       # the kernel's sources, in order

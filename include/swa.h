@@ -104,11 +104,6 @@ typedef struct {
  * with SWA_WITH_SQ) is >= 2^64, so that no entry can wrap: for uint8 this
  * never happens below 2.8e14 px; a uint16 image with Q must have fewer than
  * 4,295,098,372 px.
- * Environment variables read once per process select build variants kept
- * for measurements (the tables are the same): SWA_TICKET_ORDER=row (tiles in
- * row-major order instead of along anti-diagonals), SWA_CORNER_MIN_SLICES=n
- * (corner-record look-back for images of n or more 256-column slices),
- * SWA_SAT_VARIANT=direct (no shared-memory staging of the image tile).
  */
 swa_status swa_build_sat(const void *d_image, int64_t rows, int64_t cols,
                          int64_t pitch_bytes, swa_dtype dtype, uint32_t flags,
@@ -147,7 +142,9 @@ swa_status swa_build_count_sat(const void *d_image, int64_t rows, int64_t cols,
  *                build may overwrite.
  *   d_status     optional caller-owned device word: set to 0 by the call, and
  *                bit 0 set by the kernel if a look-back wait expired (the
- *                tables are then incomplete).  May be NULL.
+ *                tables are then incomplete).  May be NULL, but then such a
+ *                timeout cannot be observed: the bit goes to a word inside
+ *                the fixed scratch array, which the next call clears.
  * Scratch lives in one fixed 64 MiB device array inside the library, which
  * every device that loads the library holds until the process exits.  An
  * image needing more (about 100 million uint8 or 58 million uint16
@@ -209,6 +206,16 @@ swa_status swa_sat_bytes(int64_t rows, int64_t cols, swa_dtype dtype, uint32_t f
 /* Wait for the handle's work on its home stream and on every stream a later
  * call used, then report any error the device recorded (SWA_ETIMEOUT). */
 swa_status swa_sync(const swa_sat *sat);
+
+/* The device error word of the handle's build, read without waiting for any
+ * stream (a 4-byte copy on a private non-blocking stream): SWA_ETIMEOUT if a
+ * look-back wait of the build expired (the tables are then incomplete), else
+ * SWA_OK.  The caller must already know that the build has finished, e.g.
+ * from an event recorded after it (or after a later call on the handle's
+ * stream) that has completed; before that the answer may be stale.  For
+ * request loops that cannot drain a busy stream with swa_sync.  No paper
+ * counterpart (error reporting of the bounded waits). */
+swa_status swa_sat_status(const swa_sat *sat);
 
 /* Release S and Q, stream-ordered on the handle's home stream after every
  * call made on the handle.  NULL is a no-op; a handle that was already freed

@@ -15,6 +15,9 @@ definitions and the paper sections they follow):
 - ``window_sliding`` DP-naive-SWA read as separable moving sums (Section IV-A)
 - ``window_one``     one window by the definition (sampled checks at any size)
 - ``window_sat_rows`` integral-image SWA for selected output rows
+- ``window_rows_stream`` the same from the image, streamed once, keeping only
+                     the table rows the windows' corners lie on (full-size
+                     checks without whole tables in host memory)
 - ``stats_from_moments`` mean and population std from exact integer moments
 - ``count_brute``    threshold count map by the definition (pixels > thr per
                      window, their fraction and the indicator's std)
@@ -77,6 +80,8 @@ def _load():
         lib.oracle_stats_bulk.restype = None
         lib.oracle_window_sat_rows.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, i64,
                                                vp, i64, vp, vp, vp, i64]
+        lib.oracle_window_rows_stream.argtypes = [vp, i64, i64, i64, ci, i64, i64, i64, i64,
+                                                  vp, i64, vp, vp, vp, i64]
         _lib = lib
     return _lib
 
@@ -220,6 +225,21 @@ def window_sat_rows(S, Q, wh, ww, sy, sx, out_rows, outputs=("sum", "mean", "std
     _check(_load().oracle_window_sat_rows(S.ctypes.data, _p(Q), c, r, c, wh, ww, sy, sx,
                                           rr.ctypes.data, len(rr), _p(s), _p(m), _p(d), C),
            "window_sat_rows")
+    return {k: v for k, v in (("sum", s), ("mean", m), ("std", d)) if v is not None}
+
+
+def window_rows_stream(img, wh, ww, sy, sx, out_rows, outputs=("sum", "mean", "std")):
+    """Integral-image SWA for the selected (strictly increasing) output rows,
+    from the image streamed once: only the table rows the corners lie on are
+    kept, so this works on images whose tables exceed host memory."""
+    img, dt = _img(img)
+    r, c = img.shape
+    R, C = window_shape(r, c, wh, ww, sy, sx)
+    rr = np.ascontiguousarray(np.asarray(out_rows, dtype=np.int64))
+    s, m, d = _outputs(len(rr), C, outputs)
+    _check(_load().oracle_window_rows_stream(img.ctypes.data, r, c, img.strides[0], dt, wh, ww,
+                                             sy, sx, rr.ctypes.data, len(rr), _p(s), _p(m),
+                                             _p(d), C), "window_rows_stream")
     return {k: v for k, v in (("sum", s), ("mean", m), ("std", d)) if v is not None}
 
 

@@ -402,3 +402,104 @@ int oracle_count_brute(const void *img, int64_t rows, int64_t cols, int64_t pitc
         }
     return OK;
 }
+
+/*
+ * Integral-image SWA for selected output rows of an image whose tables need
+ * not fit in host memory (the row-streaming reading of Section II-B): the
+ * image is read once from the top while the running table rows of S and Q
+ * (column sums of the row prefix sums) are kept; as the stream passes a table
+ * row that a requested window's corners lie on -- row y0 - 1 or row
+ * y0 + wh - 1 of a requested output row -- that row is copied out.  The four
+ * lookups of oracle_window_sat are then made on the copied rows (index -1
+ * reading as 0).  out_rows must be strictly increasing; row k of the outputs
+ * (ld entries apart) receives output row out_rows[k].  Q is formed only when
+ * std is requested.
+ */
+static int64_t find_row(const int64_t *need, int64_t nn, int64_t y)
+{
+    int64_t lo = 0, hi = nn - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (need[mid] < y) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+int oracle_window_rows_stream(const void *img, int64_t rows, int64_t cols, int64_t pitch,
+                              int dtype, int64_t wh, int64_t ww, int64_t sy, int64_t sx,
+                              const int64_t *out_rows, int64_t nrows, uint64_t *sum,
+                              double *mean, double *std, int64_t ld)
+{
+    int64_t R, C;
+    if (!args_ok(img, rows, cols, pitch, dtype) || !out_rows || nrows < 0) return E_ARG;
+    if (oracle_window_shape(rows, cols, wh, ww, sy, sx, &R, &C) != OK) return E_ARG;
+    if (ld < C) return E_ARG;
+    for (int64_t k = 0; k < nrows; ++k)
+        if (out_rows[k] < 0 || out_rows[k] >= R || (k && out_rows[k] <= out_rows[k - 1]))
+            return E_ARG;
+    if (nrows == 0) return OK;
+    const int with_q = std != NULL;
+    if (!oracle_fits_u64(rows, cols, dtype, with_q)) return E_OVERFLOW;
+    /* The table rows the corners lie on, increasing and distinct: a merge of
+     * the top rows (y0 - 1, when y0 > 0) and the bottom rows (y0 + wh - 1). */
+    int64_t *need = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * nrows));
+    if (!need) return E_MEM;
+    int64_t nn = 0, a = 0, b = 0;
+    while (a < nrows || b < nrows) {
+        int64_t top = a < nrows ? out_rows[a] * sy - 1 : INT64_MAX;
+        int64_t bot = b < nrows ? out_rows[b] * sy + wh - 1 : INT64_MAX;
+        if (top < 0) { ++a; continue; }
+        int64_t y = top < bot ? top : bot;
+        if (top == y) ++a;
+        if (bot == y) ++b;
+        if (!nn || need[nn - 1] != y) need[nn++] = y;
+    }
+    uint64_t *s = (uint64_t *)calloc((size_t)cols, sizeof(uint64_t));
+    uint64_t *q = (uint64_t *)calloc((size_t)cols, sizeof(uint64_t));
+    uint64_t *Ss = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nn * cols));
+    uint64_t *Qs = with_q ? (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nn * cols)) : NULL;
+    if (!s || !q || !Ss || (with_q && !Qs)) {
+        free(need); free(s); free(q); free(Ss); free(Qs);
+        return E_MEM;
+    }
+    int64_t k = 0;
+    for (int64_t y = 0; y <= need[nn - 1]; ++y) {
+        uint64_t rs = 0, rq = 0;
+        for (int64_t x = 0; x < cols; ++x) {
+            uint64_t v = pix(img, pitch, dtype, y, x);
+            rs += v;
+            s[x] += rs;
+            if (with_q) {
+                rq += v * v;
+                q[x] += rq;
+            }
+        }
+        if (y == need[k]) {
+            memcpy(Ss + k * cols, s, sizeof(uint64_t) * (size_t)cols);
+            if (with_q) memcpy(Qs + k * cols, q, sizeof(uint64_t) * (size_t)cols);
+            ++k;
+        }
+    }
+    const uint64_t n = (uint64_t)(wh * ww);
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t i = out_rows[r], y0 = i * sy, y1 = y0 + wh - 1;
+        /* saved row of table row y1, and of y0 - 1 (-1 when y0 == 0) */
+        const int64_t kb = find_row(need, nn, y1);
+        const int64_t kt = y0 > 0 ? find_row(need, nn, y0 - 1) : -1;
+        for (int64_t j = 0; j < C; ++j) {
+            const int64_t x0 = j * sx, x1 = x0 + ww - 1;
+            uint64_t sw = at(Ss, cols, kb, x1) - at(Ss, cols, kt, x1)
+                        - at(Ss, cols, kb, x0 - 1) + at(Ss, cols, kt, x0 - 1);
+            uint64_t qw = 0;
+            if (with_q)
+                qw = at(Qs, cols, kb, x1) - at(Qs, cols, kt, x1)
+                   - at(Qs, cols, kb, x0 - 1) + at(Qs, cols, kt, x0 - 1);
+            if (sum) sum[r * ld + j] = sw;
+            oracle_stats_from_moments(n, sw, qw, mean ? &mean[r * ld + j] : NULL,
+                                      std ? &std[r * ld + j] : NULL);
+        }
+    }
+    free(need); free(s); free(q); free(Ss); free(Qs);
+    return OK;
+}

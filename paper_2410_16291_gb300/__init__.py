@@ -66,6 +66,7 @@ SIGNATURES = {
     "swa_sat_info": (ctypes.c_int, [_VP, _P(_I64), _P(_I64), _P(_I32), _P(_U32)]),
     "swa_sat_bytes": (ctypes.c_int, [_I64, _I64, ctypes.c_int, _U32, _P(_I64), _P(_I64)]),
     "swa_sync": (ctypes.c_int, [_VP]),
+    "swa_sat_status": (ctypes.c_int, [_VP]),
     "swa_free": (None, [_VP]),
     "swa_analyze": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _P(swa_window), _I32, _VP]),
     "swa_analyze_banded": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _P(swa_window), _I32,
@@ -236,6 +237,11 @@ class SAT:
 
     def sync(self):
         check(lib().swa_sync(self.handle), "swa_sync")
+
+    def status(self):
+        """The build's status code (SWA_OK or SWA_ETIMEOUT) without waiting:
+        call it only once the build is known to have finished."""
+        return int(lib().swa_sat_status(self.handle))
 
     def free(self):
         if self.handle:

@@ -293,15 +293,14 @@ k_scan(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
     __syncwarp();
 }
 
-template <typename T, bool WQ, bool VEC, int TH, int W, bool DIRECT, bool THR>
+template <typename T, bool WQ, bool VEC, int TH, int W, bool THR>
 __global__ void __launch_bounds__(W * 32, 1)
 k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
           const __grid_constant__ CUtensorMap tmQ)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
-    WarpRes w = DIRECT ? warp_res<T, TH>(smem_raw, direct_warp_bytes())
-                       : warp_res<T, TH, WQ>(smem_raw);
+    WarpRes w = warp_res<T, TH, WQ>(smem_raw);
     TileCtx c;
     c.img = a.img;
     c.pitch = a.pitch;
@@ -329,9 +328,7 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
         if ((int64_t)t >= ntiles || *(volatile uint32_t *)a.err) break;
         if (t == 0 && a.stall_tile0) continue;
         const uint32_t tile = a.diag ? diag_tile(t, a.nby, a.nsx) : t;
-        const bool ok = DIRECT ? onepass_tile_direct<T, WQ, VEC, TH>(c, tile, a.err, w)
-                               : onepass_tile<T, WQ, VEC, TH, THR>(c, tile, a.err, w);
-        if (!ok) break;
+        if (!onepass_tile<T, WQ, VEC, TH, THR>(c, tile, a.err, w)) break;
     }
     cp_async_wait_all();
     if (lane == 0) bulk_wait_all();
@@ -408,9 +405,6 @@ swa_status dispatch_twopass(const BuildPlan &p, const char *img, uint64_t *S, ui
 }
 
 template <typename T> constexpr int onepass_rows() { return sizeof(T) == 1 ? 64 : 32; }
-// Rows per tile of the direct variant (no staging, so taller tiles fit).
-template <typename T> constexpr int direct_rows() { return sizeof(T) == 1 ? 128 : 64; }
-constexpr int kDirectWarps = 16;
 
 // Warps per block of the single-pass build: as many independent warps as
 // the shared memory of one SM holds (227 KB per block, 1 KB for alignment),
@@ -423,12 +417,12 @@ template <typename T, bool WQ> constexpr int onepass_warps()
                : 16;
 }
 
-template <typename T, bool WQ, bool VEC, bool DIRECT, bool THR = false>
+template <typename T, bool WQ, bool VEC, bool THR = false>
 swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
                           char *scratch, uint32_t *err, cudaStream_t st)
 {
-    constexpr int TH = DIRECT ? direct_rows<T>() : onepass_rows<T>();
-    constexpr int W = DIRECT ? kDirectWarps : onepass_warps<T, WQ>();
+    constexpr int TH = onepass_rows<T>();
+    constexpr int W = onepass_warps<T, WQ>();
     OnePass a;
     a.img = img;
     a.pitch = p.pitch;
@@ -458,9 +452,8 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
                   (long long)p.ld);
         return SWA_ECUDA;
     }
-    const size_t smem =
-        1024 + (size_t)W * (DIRECT ? direct_warp_bytes() : onepass_warp_bytes<T, TH, WQ>());
-    auto kern = k_onepass<T, WQ, VEC, TH, W, DIRECT, THR>;
+    const size_t smem = 1024 + (size_t)W * onepass_warp_bytes<T, TH, WQ>();
+    auto kern = k_onepass<T, WQ, VEC, TH, W, THR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return launch_error("cudaFuncSetAttribute", e);
@@ -489,22 +482,14 @@ template <typename T>
 swa_status dispatch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
                             char *scratch, uint32_t *err, cudaStream_t st)
 {
-    if (p.count)        // indicator table: S only, staged
-        return p.vec ? launch_onepass<T, false, true, false, true>(p, img, S, Q, scratch, err, st)
-                     : launch_onepass<T, false, false, false, true>(p, img, S, Q, scratch, err,
-                                                                    st);
-    if (p.direct) {
-        if (p.with_q)
-            return p.vec ? launch_onepass<T, true, true, true>(p, img, S, Q, scratch, err, st)
-                         : launch_onepass<T, true, false, true>(p, img, S, Q, scratch, err, st);
+    if (p.count)        // indicator table: S only
         return p.vec ? launch_onepass<T, false, true, true>(p, img, S, Q, scratch, err, st)
                      : launch_onepass<T, false, false, true>(p, img, S, Q, scratch, err, st);
-    }
     if (p.with_q)
-        return p.vec ? launch_onepass<T, true, true, false>(p, img, S, Q, scratch, err, st)
-                     : launch_onepass<T, true, false, false>(p, img, S, Q, scratch, err, st);
-    return p.vec ? launch_onepass<T, false, true, false>(p, img, S, Q, scratch, err, st)
-                 : launch_onepass<T, false, false, false>(p, img, S, Q, scratch, err, st);
+        return p.vec ? launch_onepass<T, true, true>(p, img, S, Q, scratch, err, st)
+                     : launch_onepass<T, true, false>(p, img, S, Q, scratch, err, st);
+    return p.vec ? launch_onepass<T, false, true>(p, img, S, Q, scratch, err, st)
+                 : launch_onepass<T, false, false>(p, img, S, Q, scratch, err, st);
 }
 
 int64_t align256(int64_t v) { return (v + 255) & ~(int64_t)255; }
@@ -526,14 +511,9 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
     // address and the pitch aligned to the vector size.
     const int64_t vbytes = dtype == SWA_U8 ? 8 : 16;
     p.vec = ((uintptr_t)image % vbytes == 0) && (pitch % vbytes == 0);
-    // Single-pass variant: staged tiles by default; SWA_SAT_VARIANT=direct
-    // selects the variant that reads each tile twice instead (an ablation).
-    const char *var = getenv("SWA_SAT_VARIANT");
     p.count = (flags & kCountPlan) != 0;
-    p.direct = !p.twopass && !p.count && var && strcmp(var, "direct") == 0;
-    p.th = p.twopass  ? kTH
-           : p.direct ? (dtype == SWA_U8 ? direct_rows<uint8_t>() : direct_rows<uint16_t>())
-                      : (dtype == SWA_U8 ? onepass_rows<uint8_t>() : onepass_rows<uint16_t>());
+    p.th = p.twopass ? kTH
+                     : (dtype == SWA_U8 ? onepass_rows<uint8_t>() : onepass_rows<uint16_t>());
     p.nby = (rows + p.th - 1) / p.th;
     p.nsx = (cols + kSliceCols - 1) / kSliceCols;
     p.corner = corner_mode_for(p.nsx, dtype);
@@ -568,30 +548,16 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
 }
 
 // Ticket order of the single-pass builds: anti-diagonals (diag_tile) unless
-// SWA_TICKET_ORDER=row (or the SWA_HOOK_ROW_ORDER test hook) asks for
-// row-major order.
-bool ticket_order_diag()
-{
-    static const bool env_row = [] {
-        const char *v = getenv("SWA_TICKET_ORDER");
-        return v && strcmp(v, "row") == 0;
-    }();
-    return !env_row && !(test_hooks() & SWA_HOOK_ROW_ORDER);
-}
+// the SWA_HOOK_ROW_ORDER test hook asks for row-major order.
+bool ticket_order_diag() { return !(test_hooks() & SWA_HOOK_ROW_ORDER); }
 
 // Corner or edge mode for an image of nsx column slices.  With diagonal
 // tickets edge mode measured at least as fast at every width (uint8 and
 // uint16, 64 to 512 slices), so it is the default; with row-major tickets
-// corner mode wins from kCornerMinSlices{U8,U16} slices.
-// SWA_CORNER_MIN_SLICES=n forces corner mode from n slices, the
-// SWA_HOOK_CORNER_MODE test hook at every width.
+// corner mode wins from kCornerMinSlices{U8,U16} slices.  The
+// SWA_HOOK_CORNER_MODE test hook forces corner mode at every width.
 bool corner_mode_for(int64_t nsx, int dtype)
 {
-    static const int64_t forced = [] {
-        const char *v = getenv("SWA_CORNER_MIN_SLICES");
-        return v && *v ? (int64_t)atoll(v) : (int64_t)0;
-    }();
-    if (forced > 0) return nsx >= forced;
     if (test_hooks() & SWA_HOOK_CORNER_MODE) return true;
     if (ticket_order_diag()) return false;
     return nsx >= (dtype == SWA_U8 ? kCornerMinSlicesU8 : kCornerMinSlicesU16);
@@ -669,9 +635,14 @@ extern "C" swa_status swa_build_sat_noalloc(const void *d_image, int64_t rows, i
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    if (e != cudaSuccess) {
         set_error("cudaGetDevice: %s", cudaGetErrorString(e));
         return SWA_ECUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("device ordinal %d beyond the no-alloc table (%d devices)", dev,
+                  kNoAllocMaxDevices);
+        return SWA_EINVAL;
     }
     char *scratch = nullptr;
     {

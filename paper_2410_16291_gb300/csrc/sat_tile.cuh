@@ -857,122 +857,6 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     return true;
 }
 
-// Process tile t of one image (single pass) without staging it in shared
-// memory: the reduction reads the tile's rows from global memory (PF rows in
-// flight), the look-back is the same as above, and the scan reads the rows
-// again (mostly from L2, which still holds them).  Shared memory per warp is
-// the output ring alone, so more warps fit on an SM.  Returns false if a
-// wait gave up.
-template <typename T, bool WQ, bool VEC, int TH>
-__device__ __forceinline__ bool onepass_tile_direct(const TileCtx &a, uint32_t t, uint32_t *err,
-                                                    WarpRes &w)
-{
-    using QA = typename QAcc<T>::type;
-    constexpr int RPL = TH / 32;
-    constexpr int PF = 8;                              // rows in flight in the reduction
-    const int lane = threadIdx.x & 31;
-    const int64_t b = t / a.nsx, s = t % a.nsx;
-    const int64_t y0 = b * TH;
-    const int nr = (int)min((int64_t)TH, a.rows - y0);
-    const int64_t x = s * kSliceCols + lane * kPxPerLane;
-    auto load = [&](int r) -> Raw8<T> {
-        if (r < nr) return load_raw8<T, VEC>(a.img, a.pitch, y0 + r, x, a.cols);
-        Raw8<T> z;
-#pragma unroll
-        for (int i = 0; i < (int)sizeof(T) * 2; ++i) z.w[i] = 0;
-        return z;
-    };
-
-    // Reduce: column sums (8 per lane), row sums (lane keeps rows lane + 32 j).
-    uint64_t cs[8], cq[8];
-    uint64_t rs_s[RPL], rs_q[RPL];
-    {
-        uint32_t c32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        Raw8<T> q[PF];                                 // rows r .. r+PF-1, shifted along
-#pragma unroll
-        for (int i = 0; i < PF; ++i) q[i] = load(i);
-#pragma unroll
-        for (int j = 0; j < RPL; ++j) {
-            rs_s[j] = 0;
-            rs_q[j] = 0;
-            const int rend = min(nr, 32 * (j + 1));
-            for (int r = 32 * j; r < rend; ++r) {
-                uint32_t px[8];
-                unpack8<T>(q[0], px);
-#pragma unroll
-                for (int i = 0; i + 1 < PF; ++i) q[i] = q[i + 1];
-                q[PF - 1] = load(r + PF);
-                uint32_t rsum = 0;
-                QA rq = 0;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    c32[k] += px[k];
-                    rsum += px[k];
-                    if (WQ) {
-                        const QA p2 = (QA)px[k] * (QA)px[k];
-                        cqa[k] += p2;
-                        rq += p2;
-                    }
-                }
-                const uint64_t row_s = warp_sum(rsum);
-                const uint64_t row_q = WQ ? (uint64_t)warp_sum(rq) : 0;
-                if ((r & 31) == lane) { rs_s[j] = row_s; rs_q[j] = row_q; }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) { cs[k] = c32[k]; cq[k] = cqa[k]; }
-    }
-
-    uint64_t vs[8], vq[8], lr_s[RPL], lr_q[RPL];
-    if (!lookback_tile<WQ, TH>(a, t, b, s, cs, cq, rs_s, rs_q, err, vs, vq, lr_s, lr_q))
-        return false;
-
-    // Scan, reading the rows again (two in flight): S = K + H[y] + V*[x] + lp.
-    uint32_t cp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint64_t H_s = 0, H_q = 0;
-    const int c1 = (int)(s * (kSliceCols / 16));
-    Raw8<T> pa = load(0), pb = load(1);
-#pragma unroll
-    for (int j = 0; j < RPL; ++j) {
-        const uint64_t ls = lr_s[j], lq = lr_q[j];
-        const int rend = min(nr, 32 * (j + 1));
-        for (int r = 32 * j; r < rend; ++r) {
-            uint32_t px[8];
-            unpack8<T>(pa, px);
-            pa = pb;
-            pb = load(r + 2);
-            H_s += __shfl_sync(kFull, ls, r & 31);
-            if (WQ) H_q += __shfl_sync(kFull, lq, r & 31);
-            uint32_t lp[8];
-            QA lq8[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                cp[k] += px[k];
-                lp[k] = cp[k] + (k ? lp[k - 1] : 0u);
-                if (WQ) {
-                    cqa[k] += (QA)px[k] * (QA)px[k];
-                    lq8[k] = cqa[k] + (k ? lq8[k - 1] : (QA)0);
-                }
-            }
-            const uint32_t is = warp_incl_scan(lp[7], lane);
-            const uint64_t base_s = H_s + (uint64_t)(is - lp[7]);
-            uint64_t base_q = 0;
-            if (WQ) {
-                const QA iq = warp_incl_scan(lq8[7], lane);
-                base_q = H_q + (uint64_t)(iq - lq8[7]);
-            }
-            emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_s, vs, lp, base_q, vq, lq8, a.tmS, a.tmQ,
-                             c1, (int)(y0 + r), w.pol);
-        }
-    }
-    return true;
-}
-
-// Shared-memory bytes per warp of the direct tile routine: the ring alone.
-constexpr int direct_warp_bytes() { return ring_bytes<true>(); }
-
 // Shared-memory bytes per warp of the single-pass tile routine (a build
 // without Q keeps a ring of S rows only, so more warps fit on an SM).
 template <typename T, int TH, bool WQ = true>

@@ -542,6 +542,36 @@ swa_status swa_sync(const swa_sat *sat)
     return SWA_OK;
 }
 
+swa_status swa_sat_status(const swa_sat *sat)
+{
+    if (!live(sat)) return SWA_EINVAL;
+    const Handle *h = reinterpret_cast<const Handle *>(sat);
+    // A private non-blocking stream per thread, so that the read neither
+    // waits for nor joins any other stream's work (the legacy default stream
+    // would wait for every blocking stream).
+    static thread_local cudaStream_t qs[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device ordinal %d beyond the library's table of %d", dev, kMaxDevices);
+        return SWA_EINVAL;
+    }
+    if (!qs[dev] && (e = cudaStreamCreateWithFlags(&qs[dev], cudaStreamNonBlocking)) !=
+                        cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreateWithFlags");
+    uint32_t err = 0;
+    if ((e = cudaMemcpyAsync(&err, h->d_err, sizeof(err), cudaMemcpyDeviceToHost, qs[dev])) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(qs[dev])) != cudaSuccess)
+        return cuda_fail(e, "reading the device error word");
+    if (err & kErrTimeout) {
+        set_error("a look-back wait exceeded its limit");
+        return SWA_ETIMEOUT;
+    }
+    return SWA_OK;
+}
+
 void swa_free(swa_sat *sat)
 {
     if (!sat) return;

@@ -32,7 +32,6 @@ struct BuildPlan {
     // scratch layout (byte offsets inside one allocation)
     int64_t off_err, off_cs, off_rs, off_bt, off_stat, off_ticket, scratch_bytes;
     bool twopass;
-    bool direct;          // single pass reading the tile twice instead of staging it
     bool count;           // table of the indicator "pixel > thr" (S only)
     uint32_t thr;
     bool corner;          // single pass: corner term from corner records (wide images)
@@ -83,12 +82,11 @@ bool fits_u64(int64_t rows, int64_t cols, int dtype, bool with_q);
 constexpr uint32_t kCountPlan = 1u << 31;
 // Single-pass look-back mode for an image nsx column slices wide: edge mode
 // with diagonal tickets; with row-major tickets corner records from the
-// dtype's threshold on.  SWA_CORNER_MIN_SLICES=n (corner mode from n slices)
-// and the SWA_HOOK_CORNER_MODE test hook override it.
+// dtype's threshold on.  The SWA_HOOK_CORNER_MODE test hook forces corner
+// mode.
 bool corner_mode_for(int64_t nsx, int dtype);
 // Ticket order of the single-pass builds: anti-diagonals unless the
-// environment variable SWA_TICKET_ORDER is "row" or the SWA_HOOK_ROW_ORDER
-// test hook is set.
+// SWA_HOOK_ROW_ORDER test hook is set.
 bool ticket_order_diag();
 BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype,
                     uint32_t flags, const void *image);

@@ -14,7 +14,12 @@ list of windows.  The server
   build on the device instead of building again);
 - runs admitted requests on a small set of CUDA streams, so the builds and
   queries of different requests overlap on the device;
-- records, per request, the time from arrival to completion.
+- records, per request, the time from arrival to completion;
+- checks every build's device status when its first request completes: a
+  build whose bounded look-back wait expired (``SWA_ETIMEOUT``) is dropped
+  from the cache, and every request served from it is reported failed
+  (``Request.error``) instead of completed;
+- rejects, by itself, a request that could never fit the budget.
 
 ``plain_path`` runs the same requests the plain way for comparison: one at a
 time on one stream, uploading, building, querying and freeing the tables of
@@ -46,6 +51,11 @@ class Request:
     done: float = None
     hit: bool = False
     bypassed: int = 0            # younger requests admitted while this one waited
+    error: str = None            # set when the request failed (results not valid)
+
+    @property
+    def failed(self):
+        return self.error is not None
 
     @property
     def latency(self):
@@ -58,6 +68,8 @@ class _Entry:
     nbytes: int
     ready: object = None         # torch.cuda.Event recorded after the build
     refs: int = 0
+    status: int = None           # the build's status once read (swa.SWA_OK, ...)
+    dropped: bool = False        # out of the cache; freed when refs reaches 0
 
 
 class TableCache:
@@ -106,6 +118,20 @@ class TableCache:
         """Cache a built table whose bytes were already reserved."""
         self.entries[key] = entry
 
+    def drop(self, key, entry: _Entry):
+        """Take a table out of the cache (a failed build): no later request
+        finds it; its memory goes back once no in-flight request uses it."""
+        if self.entries.get(key) is entry:
+            del self.entries[key]
+        entry.dropped = True
+        self.release_dropped(entry)
+
+    def release_dropped(self, entry: _Entry):
+        if entry.dropped and not entry.refs and entry.sat is not None:
+            entry.sat.free()
+            entry.sat = None
+            self.used -= entry.nbytes
+
     def release(self, nbytes: int):
         self.used -= nbytes
 
@@ -144,12 +170,22 @@ class Server:
     slots: maximum number of requests on the device at once.
     lookahead, max_bypass: admission may skip over a request that does not
     fit yet (see ``_admit``).
+    keep_results: keep each request's output tensors in ``Request.result``
+    after it completes (they are outside the budget from then on).
+    on_complete: optional ``f(request)`` called on the host as each request
+    finishes (failed ones included), before its results are dropped: the
+    place for a client to copy or reduce them.  Work it enqueues on the
+    device must run on the current stream; the output tensors are released
+    to PyTorch's allocator right after the call, so the callback marks them
+    (``Tensor.record_stream``) if it uses them on another stream.
     """
 
     def __init__(self, budget_bytes: int, streams: int = 4, slots: int = 8,
-                 keep_results: bool = True, lookahead: int = 8, max_bypass: int = 16):
+                 keep_results: bool = True, lookahead: int = 8, max_bypass: int = 16,
+                 on_complete=None):
         import torch
         self.keep_results = keep_results
+        self.on_complete = on_complete
         self.torch = torch
         self.budget = int(budget_bytes)
         if isinstance(streams, int):
@@ -162,7 +198,8 @@ class Server:
         self.cache = TableCache(budget_bytes)
         self.inflight = []           # (request, event, transient_bytes, entry, image_tensor)
         self.waiting = collections.deque()
-        self.completed = []
+        self.completed = []          # every finished request, failed ones included
+        self.failed = []             # the failed ones (Request.error says why)
         self.hits = 0
         self.misses = 0
         self._rr = 0
@@ -172,7 +209,9 @@ class Server:
         return self.cache.evictions
 
     # ----------------------------------------------------------- dispatch --
-    def _try_admit(self, req: Request, now: float) -> bool:
+    def _try_admit(self, req: Request, now: float):
+        """True if admitted, False if it does not fit yet, None if it can
+        never fit the budget."""
         torch = self.torch
         rows, cols = req.host_image.shape
         code = swa._dtype_code(req.host_image)
@@ -187,8 +226,8 @@ class Server:
             img_b = rows * cols * req.host_image.element_size()
             transient = out_b + scr_b + img_b
             if tab_b + transient > self.budget:
-                raise MemoryError("request %d needs %d bytes, budget %d" %
-                                  (req.rid, tab_b + transient, self.budget))
+                req.error = "needs %d bytes, budget %d" % (tab_b + transient, self.budget)
+                return None
             if not self.cache.reserve(tab_b + transient):
                 return False
         s = self.streams[self._rr % len(self.streams)]
@@ -215,16 +254,34 @@ class Server:
         self.inflight.append((req, ev, transient, entry, img_dev))
         return True
 
+    def _finish(self, req: Request, now: float):
+        req.done = now
+        if self.on_complete is not None:
+            self.on_complete(req)
+        if req.failed:
+            req.result = None
+            self.failed.append(req)
+        elif not self.keep_results:
+            req.result = None
+        self.completed.append(req)
+
     def _poll(self, now: float):
         still = []
         for req, ev, transient, entry, img_dev in self.inflight:
             if ev.query():
-                req.done = now
+                # The build finished before this request's queries did: read
+                # its device status once (no stream is drained).
+                if entry.status is None:
+                    entry.status = entry.sat.status()
+                    if entry.status != swa.SWA_OK:
+                        self.cache.drop(req.image_id, entry)
+                if entry.status != swa.SWA_OK:
+                    req.error = "table build failed: %s" % (
+                        swa.lib().swa_status_str(entry.status).decode())
                 entry.refs -= 1
                 self.cache.release(transient)
-                if not self.keep_results:
-                    req.result = None
-                self.completed.append(req)
+                self.cache.release_dropped(entry)
+                self._finish(req, now)
             else:
                 still.append((req, ev, transient, entry, img_dev))
         self.inflight = still
@@ -239,7 +296,13 @@ class Server:
         progressed = False
         while self.waiting and len(self.inflight) < self.slots:
             head = self.waiting[0]
-            if self._try_admit(head, now):
+            ok = self._try_admit(head, now)
+            if ok is None:                      # can never fit: fail it alone
+                self.waiting.popleft()
+                self._finish(head, now)
+                progressed = True
+                continue
+            if ok:
                 self.waiting.popleft()
                 progressed = True
                 continue
@@ -247,13 +310,18 @@ class Server:
                 break
             admitted = None
             for i in range(1, min(len(self.waiting), 1 + self.lookahead)):
-                if self._try_admit(self.waiting[i], now):
+                ok = self._try_admit(self.waiting[i], now)
+                if ok is None:
+                    self._finish(self.waiting[i], now)
                     admitted = i
+                    break
+                if ok:
+                    admitted = i
+                    head.bypassed += 1
                     break
             if admitted is None:
                 break
             del self.waiting[admitted]
-            head.bypassed += 1
             progressed = True
         return progressed
 
@@ -300,19 +368,25 @@ def plain_path(requests, realtime: bool = True, stream=None, keep_results: bool 
             img = r.host_image.to("cuda", non_blocking=True)
             sat = swa.build_sat(img, with_sq=True, stream=s)
             r.result = sat.window_stats(r.windows, stream=s)
-            sat.free()
         s.synchronize()
+        st = sat.status()
+        sat.free()
         r.done = time.perf_counter() - t0
-        if not keep_results:
+        if st != swa.SWA_OK:
+            r.error = "table build failed: %s" % swa.lib().swa_status_str(st).decode()
+        if not keep_results or r.failed:
             r.result = None
     return time.perf_counter() - t0
 
 
 def latency_summary(requests):
-    lat = np.array([r.latency for r in requests if r.latency is not None])
+    """Latency percentiles over the requests that completed without error;
+    failed requests are counted separately."""
+    failed = sum(1 for r in requests if r.failed)
+    lat = np.array([r.latency for r in requests if r.latency is not None and not r.failed])
     if not len(lat):
-        return {}
+        return {"failed": failed} if failed else {}
     return {"p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
-            "requests": int(len(lat))}
+            "requests": int(len(lat)), "failed": failed}

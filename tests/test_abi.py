@@ -90,6 +90,7 @@ def test_build_argument_checks_before_any_device_work(L):
 def test_handle_checks(L):
     assert L.swa_window_stats(None, 2, 2, 1, 1, 1, None, None, None, 1, None) == swa.SWA_EINVAL
     assert L.swa_sync(None) == swa.SWA_EINVAL
+    assert L.swa_sat_status(None) == swa.SWA_EINVAL
     assert L.swa_sat_data(None, None, None, None) == swa.SWA_EINVAL
     bogus = ctypes.c_void_p(0xdeadbeef)
     assert L.swa_sync(bogus) == swa.SWA_EINVAL          # not a live handle: never read

@@ -5,6 +5,7 @@ size."""
 import numpy as np
 import pytest
 
+import full_parity
 import oracle
 import paper_2410_16291_gb300 as swa
 import synth
@@ -39,8 +40,9 @@ def sampled_windows(img, res, windows, n):
 
 
 def test_workload1_20k():
-    """20,000 x 20,000 u8: full S and Q, sampled full output rows and random
-    windows for w = 50, 100, 200 at stride 1."""
+    """20,000 x 20,000 u8: full S and Q, and every one of the 1,186,171,803
+    windows (w = 50, 100, 200 at stride 1) with its sum, mean and std, bit
+    for bit against the oracle; random windows also by the definition."""
     (im,) = synth.workload(1)
     img = im.generate()
     sat = swa.build_sat(to_device(img))
@@ -50,21 +52,18 @@ def test_workload1_20k():
     S, Q = sat.tables()
     np.testing.assert_array_equal(u64(S), S_ref)
     np.testing.assert_array_equal(u64(Q), Q_ref)
-    for (wh, ww, sy, sx), got in zip(wins, res):
-        R, C = got["sum"].shape
-        rows = sorted(set([0, 1, R // 2, R - 1] + list(RNG.integers(0, R, 4))))
-        want = oracle.window_sat_rows(S_ref, Q_ref, wh, ww, sy, sx, rows)
-        np.testing.assert_array_equal(u64(got["sum"][rows]), want["sum"])
-        np.testing.assert_array_equal(f64(got["mean"][rows]), want["mean"])
-        np.testing.assert_array_equal(f64(got["std"][rows]), want["std"])
+    del S_ref, Q_ref, S, Q
+    assert full_parity.check_all_windows(img, wins, res) == 1186171803
     sampled_windows(img, res, wins, 200)
     sat.free()
 
 
 def test_workload2_70k_by_85k():
     """70,000 x 85,000 u8 (5.95e9 px, 95 GB of tables): sampled table rows
-    streamed by the oracle, last entries equal the totals, sampled windows and
-    whole output rows by the definition."""
+    streamed by the oracle, last entries equal the totals, every one of the
+    45,728,608 windows (256 and 1024 at stride 16) against the oracle's
+    streamed-rows windows, sampled windows and a whole output row by the
+    definition."""
     (im,) = synth.workload(2)
     img = im.generate()
     dev = to_device(img)
@@ -79,6 +78,7 @@ def test_workload2_70k_by_85k():
     np.testing.assert_array_equal(u64(Q[rows]), Q_ref)
     tot_s, tot_q = oracle.total(img)
     assert int(S_ref[-1, -1]) == tot_s and int(Q_ref[-1, -1]) == tot_q
+    assert full_parity.check_all_windows(img, wins, res, rows_per_chunk=128) == 45728608
     sampled_windows(img, res, wins, 100)
     # one whole output row of the 256 window by the definition
     got = res[0]

@@ -72,3 +72,35 @@ def test_results_identical_alone_and_in_the_mix():
             np.testing.assert_array_equal(u64(got["sum"]), want["sum"])
             np.testing.assert_array_equal(f64(got["std"]), want["std"])
     server.close()
+
+
+def test_failed_build_is_reported_and_its_table_not_reused():
+    """A build whose look-back wait expires (the stall hook keeps the first
+    tile silent, so the bounded waits run out; nothing faults) is reported as
+    a failed request, leaves the cache, and the next request for the same
+    image builds again and gets the correct result."""
+    require_gpu()
+    import torch
+    from paper_2410_16291_gb300.serve import Request, Server
+    img = synth.intensity_u8(600, 900, 77, synth.cluster_count(600, 900))
+    host = torch.from_numpy(img).pin_memory()
+    wins = [(32, 32, 4, 4)]
+    server = Server(budget_bytes=1 << 30, streams=2, slots=4)
+    L = swa.lib()
+    L.swa_set_test_hooks(swa.SWA_HOOK_STALL_TILE0)
+    try:
+        a = Request(0, "img", host, wins)
+        server.run([a], realtime=False)
+    finally:
+        L.swa_set_test_hooks(0)
+    assert a.failed and "build failed" in a.error and a.result is None
+    assert server.failed == [a] and server.cache.get("img") is None
+    assert server.cache.used == 0
+    b = Request(1, "img", host, wins)
+    server.run([b], realtime=False)
+    assert not b.failed and not b.hit and server.misses == 2
+    S_ref, Q_ref = oracle.sat(img)
+    want = oracle.window_sat(S_ref, Q_ref, 32, 32, 4, 4)
+    np.testing.assert_array_equal(u64(b.result[0]["sum"]), want["sum"])
+    np.testing.assert_array_equal(f64(b.result[0]["std"]), want["std"])
+    server.close()

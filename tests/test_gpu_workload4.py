@@ -1,0 +1,124 @@
+"""The served workload at its stated size: a Poisson stream of 200 requests
+(mean 200 req/s) over a pool of 64 images (square sides 1,000-40,000,
+uint8/uint16 half and half, Zipf popularity), each asking 1-8 windows of
+16-1024 px at strides 4-16 with sum, mean and std, served by the
+continuous-batching server under a 120 GB budget with resident tables and
+LRU eviction.
+
+- Every result equals the same request run alone (upload, build, query on
+  one stream).  The outputs (160 GB in all) are compared through two 64-bit
+  digests of all their bits, taken on the device as each request completes:
+  the first weights element i by an odd number, so a single differing
+  element always changes it.
+- Ten requests (every 20th) keep their outputs: sampled output rows of every
+  window equal the oracle's streamed-rows windows, bit for bit.
+"""
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import full_parity
+import oracle
+import paper_2410_16291_gb300 as swa
+import synth
+from gpu_util import f64, require_gpu, u64
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+K1 = -7046029254386353131          # 0x9E3779B97F4A7C15 as int64 (odd)
+K2 = -4658895280553007687          # 0xBF58476D1CE4E5B9 as int64 (odd)
+
+
+def digest(results):
+    """Two wrap-around 64-bit digests per output array, as one device tensor.
+    Runs on the current stream."""
+    import torch
+    out = []
+    for d in results:
+        for key in ("sum", "mean", "std"):
+            x = d[key].contiguous().view(torch.int64).reshape(-1)
+            i = torch.arange(x.numel(), device=x.device, dtype=torch.int64)
+            h1 = (x * ((2 * i + 1) * K1)).sum()
+            h2 = ((x ^ (x >> 29)) * (i * K2 + K1)).sum()
+            out += [h1, h2]
+    return torch.stack(out)
+
+
+def test_workload4_served_stream_equals_alone_and_the_oracle():
+    require_gpu()
+    import torch
+    from paper_2410_16291_gb300 import build
+    from paper_2410_16291_gb300.serve import Request, Server
+    build.build()
+    pool, trace = synth.serve_requests(200, synth.DEFAULT_SEED + 4)
+    host, arrays = {}, {}
+    for _, idx, _ in trace:                  # generate straight into pinned memory
+        if idx in host:
+            continue
+        im = pool[idx]
+        if im.dtype == "u8":
+            t = torch.empty((im.rows, im.cols), dtype=torch.uint8, pin_memory=True)
+            a = t.numpy()
+        else:
+            t = torch.empty((im.rows, im.cols), dtype=torch.int16, pin_memory=True)
+            a = t.numpy().view(np.uint16)
+        im.generate(out=a)
+        host[idx], arrays[idx] = t, a
+    reqs = [Request(k, idx, host[idx], [(w.wh, w.ww, w.sy, w.sx) for w in wl], arrival=t)
+            for k, (t, idx, wl) in enumerate(trace)]
+    keep = set(range(0, 200, 20))
+    digests, kept = {}, {}
+
+    def on_complete(req):
+        if req.failed:
+            return
+        s = torch.cuda.current_stream()
+        for d in req.result:
+            for t in d.values():
+                t.record_stream(s)
+        digests[req.rid] = digest(req.result)
+        if req.rid in keep:
+            kept[req.rid] = req.result
+
+    server = Server(budget_bytes=120 * 10**9, streams=4, slots=8, keep_results=False,
+                    on_complete=on_complete)
+    server.run(reqs, realtime=True)
+    torch.cuda.synchronize()
+    assert len(server.completed) == 200 and not server.failed
+    assert server.hits > 0 and server.misses > 0 and server.evictions > 0
+    assert set(digests) == set(range(200))
+
+    s = torch.cuda.Stream()
+    for q in reqs:
+        with torch.cuda.stream(s):
+            dev = q.host_image.to("cuda", non_blocking=True)
+            sat = swa.build_sat(dev, stream=s)
+            alone = sat.window_stats(q.windows, stream=s)
+            dg = digest(alone)
+        sat.sync()
+        assert torch.equal(dg, digests[q.rid]), q.rid
+        sat.free()
+        del alone, dev
+
+    rng = np.random.default_rng(404)
+    tasks = []
+    for rid in sorted(keep):
+        q = reqs[rid]
+        for (wh, ww, sy, sx), got in zip(q.windows, kept[rid]):
+            R = got["sum"].shape[0]
+            rows = sorted(set([0, R - 1] + rng.integers(0, R, 4).tolist()))
+            tasks.append((arrays[q.image_id], (wh, ww, sy, sx), got, rows))
+
+    def check(t):
+        a, (wh, ww, sy, sx), got, rows = t
+        want = oracle.window_rows_stream(a, wh, ww, sy, sx, rows)
+        np.testing.assert_array_equal(u64(got["sum"][rows]), want["sum"])
+        np.testing.assert_array_equal(f64(got["mean"][rows]), want["mean"])
+        np.testing.assert_array_equal(f64(got["std"][rows]), want["std"])
+        return 1
+
+    with ThreadPoolExecutor(full_parity.threads()) as ex:
+        checked = sum(ex.map(check, tasks))
+    assert checked == sum(len(reqs[r].windows) for r in keep)
+    server.close()

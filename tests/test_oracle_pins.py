@@ -279,3 +279,32 @@ def test_window_sat_rows_equals_full():
     part = oracle.window_sat_rows(S, Q, 6, 5, 2, 3, rows)
     for k in ("sum", "mean", "std"):
         np.testing.assert_array_equal(part[k], full[k][rows])
+
+
+def test_window_rows_stream_equals_the_definition():
+    """The streamed-rows oracle (only the table rows the corners lie on are
+    kept) against the naive definition, on random subsets of output rows of
+    ragged images: windows as tall as the image, strides larger than the
+    window, first and last rows, both pixel types."""
+    rng = np.random.default_rng(404)
+    for it in range(300):
+        r, c = (int(v) for v in rng.integers(1, 48, 2))
+        dt = np.uint8 if it % 2 else np.uint16
+        img = rng.integers(0, 256 if dt == np.uint8 else 65536, (r, c)).astype(dt)
+        wh = int(rng.integers(1, r + 1)) if it % 7 else r
+        ww = int(rng.integers(1, c + 1))
+        sy, sx = (int(v) for v in rng.integers(1, 9, 2))
+        R, C = oracle.window_shape(r, c, wh, ww, sy, sx)
+        rows = sorted(set([0, R - 1] + rng.integers(0, R, int(rng.integers(0, R + 1))).tolist()))
+        got = oracle.window_rows_stream(img, wh, ww, sy, sx, rows)
+        want = oracle.window_brute(img, wh, ww, sy, sx)
+        for k in ("sum", "mean", "std"):
+            np.testing.assert_array_equal(got[k], want[k][rows], err_msg="%d %s" % (it, k))
+    # sum only (no squared table is formed) and argument checks
+    img = rng.integers(0, 256, (30, 40)).astype(np.uint8)
+    got = oracle.window_rows_stream(img, 5, 6, 2, 3, [1, 4], outputs=("sum",))
+    np.testing.assert_array_equal(got["sum"], oracle.window_brute(img, 5, 6, 2, 3)["sum"][[1, 4]])
+    with pytest.raises(ValueError):
+        oracle.window_rows_stream(img, 5, 6, 2, 3, [4, 1])
+    with pytest.raises(ValueError):
+        oracle.window_rows_stream(img, 5, 6, 2, 3, [13])          # R = 13 rows: 0..12

@@ -90,3 +90,51 @@ def test_admission_respects_slots_and_order():
     sv.waiting.extend(Request(i, i, None, []) for i in range(5))
     sv._admit(0.0)
     assert order == [0, 1, 2] and [r.rid for r in sv.waiting] == [3, 4]
+
+
+def test_dropped_entry_is_freed_when_its_last_user_finishes():
+    """A failed build leaves the cache at once (no later hit finds it) and
+    gives its bytes back only when no in-flight request uses it."""
+    FakeSat.freed = []
+    c = TableCache(100)
+    assert c.reserve(40)
+    e = _Entry(FakeSat("bad"), 40, refs=2)
+    c.insert("img", e)
+    c.drop("img", e)
+    assert c.get("img") is None and FakeSat.freed == [] and c.used == 40
+    e.refs = 1
+    c.release_dropped(e)
+    assert FakeSat.freed == [] and c.used == 40
+    e.refs = 0
+    c.release_dropped(e)
+    assert FakeSat.freed == ["bad"] and c.used == 0
+    c.release_dropped(e)                 # idempotent
+    assert FakeSat.freed == ["bad"] and c.used == 0
+
+
+def test_request_that_can_never_fit_fails_alone():
+    """A request larger than the whole budget is reported failed by itself;
+    the requests behind it are still admitted."""
+    sv, order, Request = _fake_server(lambda r: True)
+    sv.completed, sv.failed = [], []
+    inner = sv._try_admit
+
+    def try_admit(req, now):
+        if req.rid == 1:
+            req.error = "needs more than the budget"
+            return None
+        return inner(req, now)
+    sv._try_admit = try_admit
+    sv.keep_results = True
+    sv.waiting.extend(Request(i, i, None, []) for i in range(4))
+    assert sv._admit(0.0)
+    assert order == [0, 2, 3] and not sv.waiting
+    assert [r.rid for r in sv.failed] == [1] and sv.failed[0].done == 0.0
+
+
+def test_latency_summary_skips_failed_requests():
+    from paper_2410_16291_gb300.serve import Request, latency_summary
+    rs = [Request(i, 0, None, [], arrival=0.0, done=0.01 * (i + 1)) for i in range(4)]
+    rs[3].error = "table build failed"
+    out = latency_summary(rs)
+    assert out["requests"] == 3 and out["failed"] == 1 and out["max_ms"] == 30.0

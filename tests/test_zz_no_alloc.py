@@ -20,8 +20,10 @@ from gpu_util import require_gpu, to_device, u64
 pytestmark = pytest.mark.gpu
 
 
-def noalloc_tables(img_dev, rows, cols, dtype_code, with_sq):
-    """Caller-allocated tables (torch) filled by swa_build_sat_noalloc."""
+def noalloc_tables(img_dev, rows, cols, dtype_code, with_sq, with_status=True, want=0):
+    """Caller-allocated tables (torch) filled by swa_build_sat_noalloc; the
+    status word (starting at 7, which the call must reset) must end as
+    `want`."""
     import torch
     ld = (cols + 15) // 16 * 16
     S = torch.empty((rows, ld), dtype=torch.int64, device="cuda")
@@ -31,10 +33,11 @@ def noalloc_tables(img_dev, rows, cols, dtype_code, with_sq):
     rc = swa.lib().swa_build_sat_noalloc(
         img_dev.data_ptr(), rows, cols, img_dev.stride(0) * img_dev.element_size(), dtype_code,
         swa.SWA_WITH_SQ if with_sq else 0, S.data_ptr(), Q.data_ptr() if with_sq else None, ld,
-        status.data_ptr(), st)
+        status.data_ptr() if with_status else None, st)
     assert rc == swa.SWA_OK, swa.lib().swa_last_error()
     torch.cuda.synchronize()
-    assert int(status.item()) == 0
+    if with_status:
+        assert int(status.item()) == want
     return S[:, :cols], (Q[:, :cols] if with_sq else None)
 
 
@@ -71,3 +74,26 @@ def test_noalloc_rejects_images_beyond_its_scratch():
                                  torch.cuda.current_stream().cuda_stream)
     assert rc == swa.SWA_EINVAL
     assert b"scratch" in L.swa_last_error()
+
+
+def test_noalloc_reports_an_expired_wait_and_runs_without_a_status_word():
+    """With the stall hook (the first tile never publishes, so every bounded
+    look-back wait runs out after about 2 s; nothing faults) the status word
+    gets bit 0.  Then, hook cleared, a build with no status word at all is
+    still correct."""
+    require_gpu()
+    rng = np.random.default_rng(78)
+    img = rng.integers(0, 256, (300, 700)).astype(np.uint8)
+    dev = to_device(img)
+    L = swa.lib()
+    L.swa_set_test_hooks(swa.SWA_HOOK_STALL_TILE0)
+    try:
+        noalloc_tables(dev, 300, 700, swa.SWA_U8, True, want=1)
+    finally:
+        L.swa_set_test_hooks(0)
+    ref = swa.build_sat(dev)
+    S_ref, Q_ref = ref.tables()
+    S, Q = noalloc_tables(dev, 300, 700, swa.SWA_U8, True, with_status=False)
+    np.testing.assert_array_equal(u64(S), u64(S_ref))
+    np.testing.assert_array_equal(u64(Q), u64(Q_ref))
+    ref.free()
