@@ -58,8 +58,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload: skip the batched and served sub-records")
     ap.add_argument("--cpu-rows", type=int, default=0,
-                    help="rows of the CPU-baseline sample (0: sized to ~10 s)")
+                    help="rows of the CPU sample (0: CPU_SAMPLE_ROWS)")
     ap.add_argument("--twopass", action="store_true", help="force the two-pass SAT build")
     ap.add_argument("--shape", default="",
                     help="custom image RxC (profiling cases), e.g. 8192x8192")
@@ -208,51 +210,72 @@ def traffic_record(kernel, case=None):
 
 # --------------------------------------------------------------- CPU legs --
 
-def oracle_sample(img_rows_fn, cols, windows, rows):
-    """Time the CPU oracle on the first `rows` full-width rows of the image:
-    tables, then every window of the workload that fits."""
+# The CPU legs time the oracle on one fixed sample of the workload: its first
+# CPU_SAMPLE_ROWS full-width rows (fewer if host memory is short), so the
+# cpu_baseline record and the reference arm measure the same work.
+CPU_SAMPLE_ROWS = 16384
+
+
+def oracle_sample(sample, windows, par):
+    """Time the CPU oracle on `sample` (full-width rows of the image): tables,
+    then every window of the workload that fits.  par: the row-parallel
+    variants on all threads, else the serial oracle."""
     import oracle
-    sample = img_rows_fn(rows)
+    sat = oracle.sat_par if par else oracle.sat
+    win = oracle.window_sat_par if par else oracle.window_sat
+    rows = sample.shape[0]
     t0 = time.perf_counter()
-    S, Q = oracle.sat(sample)
+    S, Q = sat(sample)
     outs = 0
     for (wh, ww, sy, sx) in windows:
         if wh <= rows:
-            r = oracle.window_sat(S, Q, wh, ww, sy, sx)
-            outs += r["sum"].size
+            outs += win(S, Q, wh, ww, sy, sx)["sum"].size
     dt = time.perf_counter() - t0
     return sample.size, outs, dt
 
 
-def cpu_baseline(im, windows, rows):
+def cpu_sample(im, windows, rows=0):
+    """The fixed CPU sample of workload image `im` (numpy): its first `rows`
+    (default CPU_SAMPLE_ROWS) full-width rows."""
     import synth
+    free = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    free = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    rows = rows or CPU_SAMPLE_ROWS
+    if free:
+        rows = min(rows, int(free * 0.3 / (18 * im.cols)))
+    rows = max(rows, max(w[0] for w in windows))
+    rows = min(rows, im.rows)
+    gen = synth.intensity_u16 if im.dtype == "u16" else synth.intensity_u8
+    return gen(rows, im.cols, im.seed, synth.cluster_count(rows, im.cols))
 
-    def rows_fn(n):
-        gen = synth.intensity_u16 if im.dtype == "u16" else synth.intensity_u8
-        return gen(n, im.cols, im.seed, synth.cluster_count(n, im.cols))
-    if rows <= 0:
-        probe = max(1024, max(w[0] for w in windows))
-        px, _, dt = oracle_sample(rows_fn, im.cols, windows, probe)
-        rows = int(probe * 10.0 / max(dt, 1e-3))          # about 10 s of oracle work
-        free = None
-        try:
-            import psutil
-            free = psutil.virtual_memory().available
-        except ImportError:
-            try:
-                with open("/proc/meminfo") as f:
-                    for line in f:
-                        if line.startswith("MemAvailable:"):
-                            free = int(line.split()[1]) * 1024
-            except OSError:
-                pass
-        if free:
-            rows = min(rows, int(free * 0.3 / (18 * im.cols)))
-        rows = max(probe, min(rows, im.rows))
-    px, outs, dt = oracle_sample(rows_fn, im.cols, windows, rows)
-    return {"value": px / dt / 1e9, "unit": "Gpx/s", "cores": 1, "kind": "oracle",
-            "sample": "%d x %d rows of the workload's generator (%.2e px), tables + the "
-                      "workload's windows that fit, serial C, %.1f s" % (rows, im.cols, px, dt)}
+
+def cpu_baseline(im, windows, rows=0):
+    """Both CPU legs on the same sample: the serial oracle on one core and
+    its row-parallel variant on every host core."""
+    import oracle
+    sample = cpu_sample(im, windows, rows)
+    cores = oracle.par_threads(os.cpu_count() or 1)
+    oracle_sample(sample, windows, True)                 # warm-up (page faults, threads)
+    par = [oracle_sample(sample, windows, True) for _ in range(3)]
+    ser = [oracle_sample(sample, windows, False) for _ in range(2)]
+    px = sample.size
+    v_par = px * len(par) / sum(p[2] for p in par) / 1e9
+    v_ser = px * len(ser) / sum(p[2] for p in ser) / 1e9
+    return {"value": v_par, "unit": "Gpx/s", "cores": cores, "kind": "oracle",
+            "sample": "%d x %d rows of the workload's generator (%.2e px): tables + the "
+                      "workload's windows that fit (%d outputs); row-parallel oracle on %d "
+                      "threads, %d runs, %.2f s each" % (
+                          sample.shape[0], im.cols, px, par[0][1], cores, len(par),
+                          sum(p[2] for p in par) / len(par)),
+            "serial": {"value": v_ser, "unit": "Gpx/s", "cores": 1,
+                       "sample": "the same sample, serial oracle, %d runs, %.2f s each" % (
+                           len(ser), sum(p[2] for p in ser) / len(ser))}}
 
 
 def workload_of(args):
@@ -273,24 +296,21 @@ def workload_of(args):
 
 
 def run_reference(args, rank, world):
-    """The oracle on the host cores as the reference arm: each step is a
-    bounded sample (1024 full-width rows) of the workload."""
-    import synth
+    """The oracle on the host cores as the reference arm: each step is the
+    CPU baseline's fixed sample, through the row-parallel oracle on every
+    host core."""
+    import oracle
     if rank != 0:
         return
     im = workload_of(args)
     windows = [(w.wh, w.ww, w.sy, w.sx) for w in im.windows]
-    rows = max(w[0] for w in windows)
-    rows = max(rows, 1024)
-
-    def rows_fn(n):
-        gen = synth.intensity_u16 if im.dtype == "u16" else synth.intensity_u8
-        return gen(n, im.cols, im.seed, synth.cluster_count(n, im.cols))
+    sample = cpu_sample(im, windows, args.cpu_rows)
+    cores = oracle.par_threads(os.cpu_count() or 1)
     for _ in range(args.warmup):
-        oracle_sample(rows_fn, im.cols, windows, rows)
+        oracle_sample(sample, windows, True)
     tot_px, tot_out, tot_t = 0, 0, 0.0
     for _ in range(args.steps):
-        px, outs, dt = oracle_sample(rows_fn, im.cols, windows, rows)
+        px, outs, dt = oracle_sample(sample, windows, True)
         tot_px += px
         tot_out += outs
         tot_t += dt
@@ -302,8 +322,10 @@ def run_reference(args, rank, world):
             "impl": "reference",
             "config": config_of(im, windows),
             "window_outputs_per_s": tot_out / tot_t,
-            "cpu_baseline": {"value": v, "unit": "Gpx/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d x %d rows per step, serial C oracle" % (rows, im.cols)},
+            "cpu_baseline": {"value": v, "unit": "Gpx/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d x %d rows per step (the CPU baseline's sample), "
+                                       "row-parallel oracle on %d threads" % (
+                                           sample.shape[0], im.cols, cores)},
             "e2e": {"value": v, "unit": "Gpx/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -471,6 +493,20 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(im, windows, args.cpu_rows)
 
+    # The batched and served workloads, measured in the same run (one GPU,
+    # default workload only) after this workload's memory is released.
+    sub = {}
+    if world == 1 and not args.no_sub and not args.shape and args.workload == 2 and \
+            args.threshold is None:
+        del dev, host, outs
+        if e2e is not None:
+            del hout
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        swa.lib().swa_trim(0)
+        sub["batched"] = batch_measure(args, local_rank, steps=5, plain_steps=2)
+        sub["served"] = serve_measure(args, local_rank, args.requests, args.budget_gb)
+
     if rank != 0:
         return
     value = job_throughput(px, ms / 1e3, world) / 1e9
@@ -484,30 +520,27 @@ def run_ours(args, rank, world, local_rank):
             "window_outputs_per_s": world * n_out / (ms / 1e3),
             "window_outputs_per_step": n_out,
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clk, "gpu_launches": launches,
+            "clocks": clk, "gpu_launches": launches, **sub,
             "build_path": "twopass" if args.twopass else "default"}
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args, rank, world, local_rank):
+def batch_measure(args, local_rank, steps, plain_steps, n_images=0, dist=False):
     """Workload 3: 256 uneven uint8/uint16 images with 1-4 queries each, all
     built and queried by one persistent launch replayed from a CUDA graph,
     against the plain per-request path (build, query, free per image, in
-    order on one stream) on the same device-resident images and outputs."""
+    order on one stream) on the same device-resident images and outputs.
+    Returns the measurements as a dict (the batch pass's ms under ``ms``)."""
     import torch
 
     import paper_2410_16291_gb300 as swa
     import synth
-    from paper_2410_16291_gb300 import build as swa_build
     from paper_2410_16291_gb300 import tune
-    swa_build.build()
-    torch.cuda.set_device(local_rank)
-    dist = world > 1
     if dist:
         import torch.distributed as td
     imgs = synth.workload(3)
-    if args.batch_images:
-        imgs = imgs[:args.batch_images]          # a smaller batch (profiling)
+    if n_images:
+        imgs = imgs[:n_images]                    # a smaller batch (profiling)
     t0 = time.perf_counter()
     devs, wins = [], []
     for im in imgs:
@@ -523,7 +556,7 @@ def run_batch(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         b = swa.Batch(devs, wins, stream=stream, **cfg)
-        for _ in range(args.warmup):
+        for _ in range(max(3, args.warmup)):
             b.run(stream)
     stream.synchronize()
     b.sync()
@@ -535,23 +568,21 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.synchronize()
 
     clocks = Clocks(gpu_id_for_smi(local_rank))
-    if rank == 0:
-        clocks.start()
+    clocks.start()
     if dist:
         td.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             g.replay()
         e1.record(stream)
     torch.cuda.synchronize()
     b.sync()
     if dist:
         td.barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device="cuda")
-    clk = clocks.stop() if rank == 0 else None
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, device="cuda")
 
     # Plain per-request path on the same images and output buffers.
     def plain_pass():
@@ -564,12 +595,13 @@ def run_batch(args, rank, world, local_rank):
     l0 = swa.lib().swa_launch_count()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record()
-    for _ in range(args.plain_steps):
+    for _ in range(plain_steps):
         plain_pass()
     p1.record()
     torch.cuda.synchronize()
-    plain_ms = p0.elapsed_time(p1) / args.plain_steps
-    plain_launches = (swa.lib().swa_launch_count() - l0) // args.plain_steps
+    plain_ms = p0.elapsed_time(p1) / plain_steps
+    plain_launches = (swa.lib().swa_launch_count() - l0) // plain_steps
+    clk = clocks.stop()
 
     # Per-kernel device time of both paths (event-bracketed launches, outside
     # the graph): where each path spends its step.
@@ -584,65 +616,100 @@ def run_batch(args, rank, world, local_rank):
     def batch_pass():
         with torch.cuda.stream(stream):
             b.run(stream)
-    batch_kernels = per_kernel(batch_pass, max(1, args.plain_steps))
+    batch_kernels = per_kernel(batch_pass, max(1, plain_steps))
     b.sync()
-    plain_kernels = per_kernel(plain_pass, max(1, args.plain_steps))
+    plain_kernels = per_kernel(plain_pass, max(1, plain_steps))
     hbm, hbm_kind = peaks()
-    algo = sum(im.pixels * ((2 if im.dtype == "u16" else 1) + 16) for im in imgs) + 24 * n_out
+    build_algo = sum(im.pixels * ((2 if im.dtype == "u16" else 1) + 16) for im in imgs)
+    build = batch_kernels.get("batch_build", {}).get("ms_per_pass")
+    query = batch_kernels.get("batch_windows", {}).get("ms_per_pass")
+    rec = {"ms": ms, "gpx_s": px / (ms / 1e3) / 1e9,
+           "window_outputs_per_s": n_out / (ms / 1e3),
+           "images": len(imgs), "pixels": px, "window_outputs": n_out, "batch_config": cfg,
+           "launch": "one persistent build launch + one query launch per pass, replayed as "
+                     "one CUDA graph", "steps": steps,
+           "build_ms": build, "query_ms": query,
+           "build_hbm_frac": (build_algo / (build / 1e3) / 1e9 / hbm) if build else None,
+           "build_algorithmic_bytes": build_algo, "peak_kind": hbm_kind,
+           "kernels": batch_kernels,
+           "plain_path": {"ms_per_pass": plain_ms, "gpx_s": px / (plain_ms / 1e3) / 1e9,
+                          "launches_per_pass": plain_launches, "kernels": plain_kernels,
+                          "passes": plain_steps},
+           "speedup_vs_plain": plain_ms / ms, "plan_bytes": b.nbytes(),
+           "gpu_launches_per_pass": sum(v["launches"] for v in batch_kernels.values()),
+           "host_generation_s": gen_s, "clocks": clk}
+    b.free()
+    del g, b, devs
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    swa.lib().swa_trim(0)
+    return rec
+
+
+def run_batch(args, rank, world, local_rank):
+    """Workload 3 as the bench line (see batch_measure)."""
+    import torch
+
+    from paper_2410_16291_gb300 import build as swa_build
+    swa_build.build()
+    torch.cuda.set_device(local_rank)
+    rec = batch_measure(args, local_rank, args.steps, args.plain_steps, args.batch_images,
+                        dist=world > 1)
     if rank != 0:
         return
-    line = {"metric": METRIC, "value": world * px / (ms / 1e3) / 1e9, "unit": "Gpx/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic",
+    ms = rec["ms"]
+    hbm, hbm_kind = peaks()
+    algo = rec["build_algorithmic_bytes"] + 24 * rec["window_outputs"]
+    line = {"metric": METRIC, "value": world * rec["pixels"] / (ms / 1e3) / 1e9,
+            "unit": "Gpx/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "256 uneven synthetic images (sides 512-8192, aspect 0.5-2, "
                                    "uint8/uint16 50/50), 1-4 windows 16-512 px stride 1-8",
-                       "images": len(imgs), "pixels": px, "window_outputs": n_out,
-                       "batch_config": cfg,
-                       "launch": "one persistent build launch + one query launch per step, "
-                                 "replayed as one CUDA graph",
-                       "l2": "inputs larger than L2 (%.1f GB of tables)" % (16 * px / 1e9)},
-            "window_outputs_per_s": world * n_out / (ms / 1e3),
-            "kernels": batch_kernels,
-            "plain_path": {"ms_per_pass": plain_ms, "gpx_s": px / (plain_ms / 1e3) / 1e9,
-                           "launches_per_pass": plain_launches, "kernels": plain_kernels},
-            "speedup_vs_plain": plain_ms / ms,
+                       "images": rec["images"], "pixels": rec["pixels"],
+                       "window_outputs": rec["window_outputs"],
+                       "batch_config": rec["batch_config"], "launch": rec["launch"],
+                       "l2": "inputs larger than L2 (%.1f GB of tables)" % (
+                           16 * rec["pixels"] / 1e9)},
+            "window_outputs_per_s": world * rec["window_outputs"] / (ms / 1e3),
+            "kernels": rec["kernels"], "plain_path": rec["plain_path"],
+            "speedup_vs_plain": rec["speedup_vs_plain"],
             "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": algo / (ms / 1e3) / 1e9,
                          "peak": hbm, "unit": "GB/s", "frac": algo / (ms / 1e3) / 1e9 / hbm,
                          "peak_kind": hbm_kind, "algorithmic_bytes_per_launch": algo,
                          "traffic": traffic_record("k_batch")},
-            "plan_bytes": b.nbytes(),
-            "gpu_launches": args.steps * sum(v["launches"] for v in batch_kernels.values()),
-            "host_generation_s": gen_s, "clocks": clk, "cpu_baseline": None, "e2e": None}
+            "build_ms": rec["build_ms"], "query_ms": rec["query_ms"],
+            "build_hbm_frac": rec["build_hbm_frac"], "plan_bytes": rec["plan_bytes"],
+            "gpu_launches": args.steps * rec["gpu_launches_per_pass"],
+            "host_generation_s": rec["host_generation_s"], "clocks": rec["clocks"],
+            "cpu_baseline": None, "e2e": None}
     print(json.dumps(line), flush=True)
-    b.free()
 
 
-def run_serve(args, rank, world, local_rank):
+def serve_measure(args, local_rank, n_requests, budget_gb):
     """Workload 4: a Poisson request stream (200 req/s) over a pool of 64
     images (sides 1,000-40,000, uint8/uint16), each request 1-8 windows with
-    sum/mean/std, served by the continuous-batching server under a 120 GB
+    sum/mean/std, served by the continuous-batching server under an HBM
     budget with resident tables, against the plain per-request path on the
-    same trace."""
+    same trace.  Returns the measurements as a dict."""
     import torch
 
     import synth
-    from paper_2410_16291_gb300 import build as swa_build
     import paper_2410_16291_gb300 as swa
     from paper_2410_16291_gb300 import serve
-    swa_build.build()
-    torch.cuda.set_device(local_rank)
-    if rank != 0:
-        return
-    pool, trace = synth.serve_requests(args.requests, synth.DEFAULT_SEED + 4)
+    pool, trace = synth.serve_requests(n_requests, synth.DEFAULT_SEED + 4)
     t0 = time.perf_counter()
     host = {}
-    for _, idx, _ in trace:
+    for _, idx, _ in trace:                   # generated straight into pinned memory
         if idx in host:
             continue
         im = pool[idx]
-        a = im.generate()
-        t = torch.from_numpy(a.view(np.int16) if im.dtype == "u16" else a).pin_memory()
+        if im.dtype == "u16":
+            t = torch.empty((im.rows, im.cols), dtype=torch.int16, pin_memory=True)
+            im.generate(out=t.numpy().view(np.uint16))
+        else:
+            t = torch.empty((im.rows, im.cols), dtype=torch.uint8, pin_memory=True)
+            im.generate(out=t.numpy())
         host[idx] = t
     gen_s = time.perf_counter() - t0
 
@@ -661,7 +728,7 @@ def run_serve(args, rank, world, local_rank):
     plain_stream = torch.cuda.Stream()
 
     def served(realtime):
-        srv = serve.Server(int(args.budget_gb * 1e9), streams=streams, slots=8,
+        srv = serve.Server(int(budget_gb * 1e9), streams=streams, slots=8,
                            keep_results=False)
         reqs = requests()
         l0 = swa.lib().swa_launch_count()
@@ -682,31 +749,63 @@ def run_serve(args, rank, world, local_rank):
                        window_outputs_per_s=n_out / t)
     served(False)
     plain(False)
+    clocks = Clocks(gpu_id_for_smi(local_rank))
+    clocks.start()
     # closed loop (every request submitted at t=0): throughput
     t_srv_c, srv_c = served(False)
     t_plain_c, plain_c = plain(False)
     # open loop (Poisson arrivals in real time): latency
     t_srv, srv = served(True)
     t_plain, plain_rt = plain(True)
-    n = len(trace)
-    line = {"metric": METRIC, "value": px / t_srv_c / 1e9, "unit": "Gpx/s", "n_gpus": 1,
+    clk = clocks.stop()
+    rec = {"requests": len(trace), "budget_gb": budget_gb, "streams": 4, "slots": 8,
+           "image_pixels_requested": px, "window_outputs": n_out,
+           "gpx_s": px / t_srv_c / 1e9,
+           "served_closed_loop": srv_c, "plain_closed_loop": plain_c,
+           "served_realtime": srv, "plain_realtime": plain_rt,
+           "throughput_vs_plain": t_plain_c / t_srv_c,
+           "p99_vs_plain_realtime": (plain_rt.get("p99_ms", 0) / srv["p99_ms"]
+                                     if srv.get("p99_ms") else None),
+           "host_generation_s": gen_s, "clocks": clk}
+    del host
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    swa.lib().swa_trim(0)
+    return rec
+
+
+def run_serve(args, rank, world, local_rank):
+    """Workload 4 as the bench line (see serve_measure)."""
+    import torch
+
+    from paper_2410_16291_gb300 import build as swa_build
+    swa_build.build()
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    rec = serve_measure(args, local_rank, args.requests, args.budget_gb)
+    n = rec["requests"]
+    t_srv_c = rec["served_closed_loop"]["seconds"]
+    line = {"metric": METRIC, "value": rec["gpx_s"], "unit": "Gpx/s", "n_gpus": 1,
             "steps": n, "warmup": 1, "ms_per_step": t_srv_c / n * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": "served: Poisson 200 req/s over 64 images (sides "
                                    "1,000-40,000, uint8/uint16), 1-8 windows 16-1024 px, "
                                    "stride 4-16, sum/mean/std",
-                       "requests": n, "budget_gb": args.budget_gb, "streams": 4, "slots": 8,
-                       "image_pixels_requested": px, "window_outputs": n_out,
+                       "requests": n, "budget_gb": rec["budget_gb"], "streams": 4, "slots": 8,
+                       "image_pixels_requested": rec["image_pixels_requested"],
+                       "window_outputs": rec["window_outputs"],
                        "value": "closed loop: requested image pixels / makespan with "
                                 "every request submitted at once"},
-            "served_closed_loop": srv_c, "plain_closed_loop": plain_c,
-            "served_realtime": srv, "plain_realtime": plain_rt,
-            "throughput_vs_plain": t_plain_c / t_srv_c,
-            "p99_vs_plain_realtime": (plain_rt.get("p99_ms", 0) / srv["p99_ms"]
-                                      if srv.get("p99_ms") else None),
-            "host_generation_s": gen_s,
-            "window_outputs_per_s": n_out / t_srv_c, "gpu_launches": srv_c["gpu_launches"],
+            "served_closed_loop": rec["served_closed_loop"],
+            "plain_closed_loop": rec["plain_closed_loop"],
+            "served_realtime": rec["served_realtime"], "plain_realtime": rec["plain_realtime"],
+            "throughput_vs_plain": rec["throughput_vs_plain"],
+            "p99_vs_plain_realtime": rec["p99_vs_plain_realtime"],
+            "host_generation_s": rec["host_generation_s"],
+            "window_outputs_per_s": rec["window_outputs"] / t_srv_c,
+            "gpu_launches": rec["served_closed_loop"]["gpu_launches"], "clocks": rec["clocks"],
             "cpu_baseline": None, "e2e": None}
     print(json.dumps(line), flush=True)
 

@@ -22,6 +22,12 @@ definitions and the paper sections they follow):
 - ``count_brute``    threshold count map by the definition (pixels > thr per
                      window, their fraction and the indicator's std)
 - ``count_sat``      the same through the indicator image's tables
+
+Row-parallel variants for timing the CPU baseline on all host cores
+(``oracle_par.c``, OpenMP row bands; pinned equal to the serial functions):
+
+- ``sat_par``, ``window_sat_par``; ``par_threads`` sets or reads the thread
+  count
 """
 from __future__ import annotations
 
@@ -33,6 +39,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_PAR = os.path.join(_HERE, "oracle_par.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -40,13 +47,14 @@ DT = {"u8": 1, "u16": 2, np.dtype(np.uint8): 1, np.dtype(np.uint16): 2}
 
 
 def build(force: bool = False) -> str:
-    """Compile ``liboracle.so`` (gcc, serial, no fast-math, no contraction)."""
-    if force or not os.path.exists(_LIB_PATH) or (
-            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+    """Compile ``liboracle.so`` (gcc, no fast-math, no contraction; OpenMP
+    only in the row-parallel variants of ``oracle_par.c``)."""
+    if force or not os.path.exists(_LIB_PATH) or any(
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(f) for f in (_SRC, _SRC_PAR)):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         subprocess.check_call([
-            "gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
-            "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+            "gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+            "-fPIC", "-shared", _SRC, _SRC_PAR, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -80,6 +88,11 @@ def _load():
         lib.oracle_stats_bulk.restype = None
         lib.oracle_window_sat_rows.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, i64,
                                                vp, i64, vp, vp, vp, i64]
+        lib.oracle_sat_par.argtypes = [vp, i64, i64, i64, ci, vp, vp, i64]
+        lib.oracle_window_sat_par.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, i64,
+                                              vp, vp, vp, i64]
+        lib.oracle_par_threads.argtypes = [ci]
+        lib.oracle_par_threads.restype = ci
         lib.oracle_window_rows_stream.argtypes = [vp, i64, i64, i64, ci, i64, i64, i64, i64,
                                                   vp, i64, vp, vp, vp, i64]
         _lib = lib
@@ -140,6 +153,22 @@ def sat(img, with_sq: bool = True):
     _check(_load().oracle_sat(img.ctypes.data, r, c, img.strides[0], dt, S.ctypes.data,
                               Q.ctypes.data if with_sq else None, c), "sat")
     return S, Q
+
+
+def sat_par(img, with_sq: bool = True):
+    """``sat`` on all threads (row bands): the same tables."""
+    img, dt = _img(img)
+    r, c = img.shape
+    S = np.empty((r, c), np.uint64)
+    Q = np.empty((r, c), np.uint64) if with_sq else None
+    _check(_load().oracle_sat_par(img.ctypes.data, r, c, img.strides[0], dt, S.ctypes.data,
+                                  Q.ctypes.data if with_sq else None, c), "sat_par")
+    return S, Q
+
+
+def par_threads(n: int = 0) -> int:
+    """Set (n > 0) and return the thread count of the parallel variants."""
+    return int(_load().oracle_par_threads(int(n)))
 
 
 def sat_rows(img, rows_wanted, with_sq: bool = True):
@@ -210,6 +239,19 @@ def window_sat(S, Q, wh, ww, sy=1, sx=1, outputs=("sum", "mean", "std")):
     s, m, d = _outputs(R, C, outputs)
     _check(_load().oracle_window_sat(S.ctypes.data, _p(Q), c, r, c, wh, ww, sy, sx,
                                      _p(s), _p(m), _p(d), C), "window_sat")
+    return {k: v for k, v in (("sum", s), ("mean", m), ("std", d)) if v is not None}
+
+
+def window_sat_par(S, Q, wh, ww, sy=1, sx=1, outputs=("sum", "mean", "std")):
+    """``window_sat`` on all threads (output rows split): the same outputs."""
+    S = np.ascontiguousarray(S, dtype=np.uint64)
+    if Q is not None:
+        Q = np.ascontiguousarray(Q, dtype=np.uint64)
+    r, c = S.shape
+    R, C = window_shape(r, c, wh, ww, sy, sx)
+    s, m, d = _outputs(R, C, outputs)
+    _check(_load().oracle_window_sat_par(S.ctypes.data, _p(Q), c, r, c, wh, ww, sy, sx,
+                                         _p(s), _p(m), _p(d), C), "window_sat_par")
     return {k: v for k, v in (("sum", s), ("mean", m), ("std", d)) if v is not None}
 
 

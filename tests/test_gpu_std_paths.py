@@ -29,6 +29,19 @@ from gpu_util import f64, require_gpu, to_device, u64
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _release_device_memory():
+    yield
+    try:
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            swa.lib().swa_trim(0)
+    except ImportError:
+        pass
+
+
 def pixels_with_D(n, T, A):
     """n integers in [0, A] with n * sum(v^2) - (sum v)^2 == T, or None."""
     base = n * A // 2

@@ -22,6 +22,19 @@ from gpu_util import require_gpu, u64
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _release_device_memory():
+    yield
+    try:
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            swa.lib().swa_trim(0)
+    except ImportError:
+        pass
+
+
 def test_workload3_batch_every_table_and_window():
     require_gpu()
     import torch

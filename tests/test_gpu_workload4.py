@@ -26,6 +26,19 @@ from gpu_util import f64, require_gpu, u64
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
+
+@pytest.fixture(scope="module", autouse=True)
+def _release_device_memory():
+    yield
+    try:
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            swa.lib().swa_trim(0)
+    except ImportError:
+        pass
+
 K1 = -7046029254386353131          # 0x9E3779B97F4A7C15 as int64 (odd)
 K2 = -4658895280553007687          # 0xBF58476D1CE4E5B9 as int64 (odd)
 

@@ -7,6 +7,7 @@ values and brute force on tiny inputs.  A dropped term, a wrong sign or index
 or a transposed operand anywhere in the oracle fails one of them.
 """
 import math
+import os
 from decimal import Decimal, getcontext
 from fractions import Fraction
 
@@ -308,3 +309,31 @@ def test_window_rows_stream_equals_the_definition():
         oracle.window_rows_stream(img, 5, 6, 2, 3, [4, 1])
     with pytest.raises(ValueError):
         oracle.window_rows_stream(img, 5, 6, 2, 3, [13])          # R = 13 rows: 0..12
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_parallel_variants_equal_the_serial_oracle(threads):
+    """The row-band parallel table build and the row-split window pass give
+    the serial oracle's tables and outputs exactly, for band counts that do
+    and do not divide the rows (including more bands than rows)."""
+    rng = np.random.default_rng(505 + threads)
+    oracle.par_threads(threads)
+    try:
+        for (r, c), dt in [((1, 1), np.uint8), ((2, 9), np.uint16), ((7, 13), np.uint8),
+                           ((64, 33), np.uint16), ((301, 257), np.uint8),
+                           ((1000, 77), np.uint16)]:
+            img = rng.integers(0, 256 if dt == np.uint8 else 65536, (r, c)).astype(dt)
+            S, Q = oracle.sat(img)
+            Sp, Qp = oracle.sat_par(img)
+            np.testing.assert_array_equal(Sp, S)
+            np.testing.assert_array_equal(Qp, Q)
+            Sp1, none = oracle.sat_par(img, with_sq=False)
+            assert none is None
+            np.testing.assert_array_equal(Sp1, S)
+            for wh, ww, sy, sx in [(1, 1, 1, 1), (r, c, 1, 1), (max(1, r // 2), max(1, c // 3), 2, 3)]:
+                want = oracle.window_sat(S, Q, wh, ww, sy, sx)
+                got = oracle.window_sat_par(S, Q, wh, ww, sy, sx)
+                for k in want:
+                    np.testing.assert_array_equal(got[k], want[k])
+    finally:
+        oracle.par_threads(os.cpu_count() or 1)

@@ -116,7 +116,7 @@ def test_request_that_can_never_fit_fails_alone():
     """A request larger than the whole budget is reported failed by itself;
     the requests behind it are still admitted."""
     sv, order, Request = _fake_server(lambda r: True)
-    sv.completed, sv.failed = [], []
+    sv.completed, sv.failed, sv.on_complete = [], [], None
     inner = sv._try_admit
 
     def try_admit(req, now):
