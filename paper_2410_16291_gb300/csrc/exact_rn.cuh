@@ -17,9 +17,11 @@
 //     giving a 54- or 55-bit quotient and an exact remainder for the sticky
 //     bit;
 //   - square root: an FP32 reciprocal-square-root seed, two Newton
-//     corrections computed from exact integer residuals N - R^2, then an
-//     exact floor correction and rounding by comparing the remainder with R
-//     (sqrt(N) > R + 1/2  <=>  N - R^2 > R for integers).
+//     corrections computed from exact integer residuals N - R^2 (the second
+//     one rounded to the nearest integer, which leaves R within 0.51 of
+//     sqrt(N)), then one exact step to the nearest integer: R is nearest iff
+//     -R < N - R^2 <= R (sqrt(N) is an integer or irrational, never a
+//     half-integer).
 // The functions are __host__ __device__ so a CPU test can compare them with
 // the host's IEEE arithmetic bit for bit.
 #pragma once
@@ -76,10 +78,16 @@ SWA_HD float bits_to_float(uint32_t b)
 #endif
 }
 
+// Reciprocal square root seed: rsqrtf on the device (within 2 ulp); on the
+// host the correctly rounded value, which host tests may push by
+// SWA_RSQRT_TEST_ULPS ulp (a compile-time define) to cover the device's
+// error.
 SWA_HD float approx_rsqrt(float x)
 {
 #if defined(__CUDA_ARCH__)
     return rsqrtf(x);
+#elif defined(SWA_RSQRT_TEST_ULPS)
+    return (1.0f / sqrtf(x)) * (1.0f + (float)(SWA_RSQRT_TEST_ULPS) * 1.1920929e-7f);
 #else
     return 1.0f / sqrtf(x);
 #endif
@@ -111,6 +119,16 @@ SWA_HD uint32_t float_bits(float f)
     uint32_t b;
     __builtin_memcpy(&b, &f, 4);
     return b;
+#endif
+}
+
+// Signed 64-bit integer nearest to a float with |x| < 2^62 (ties to even).
+SWA_HD int64_t float_to_i64_rn(float x)
+{
+#if defined(__CUDA_ARCH__)
+    return __float2ll_rn(x);
+#else
+    return (int64_t)llrintf(x);
 #endif
 }
 
@@ -236,6 +254,30 @@ SWA_HD uint64_t div_rn(uint64_t a, int aexp, const Divisor &D)
     return ((uint64_t)(E + 1023) << 52) | (M & ((1ull << 52) - 1));
 }
 
+// div_rn for a significand of exactly 53 bits (2^52 <= a < 2^53, the square
+// root's result): the 86-bit numerator is a << 33, with no search for the
+// leading bit.
+SWA_HD uint64_t div_rn53(uint64_t a, int aexp, const Divisor &D)
+{
+    if (D.pow2) {                                  // exact: a * 2^(aexp - log2 n)
+        const int E = 52 + aexp - (31 - D.z);
+        return ((uint64_t)(E + 1023) << 52) | (a & ((1ull << 52) - 1));
+    }
+    uint32_t r = (uint32_t)(a >> 31);              // < 2^22 < d
+    const uint32_t q1 = div_2by1(r, (uint32_t)(a << 1), D, &r);
+    const uint32_t q0 = div_2by1(r, 0u, D, &r);
+    uint64_t Q = ((uint64_t)q1 << 32) | q0;        // in [2^53, 2^55)
+    uint64_t sticky = r != 0;
+    int e = 0;
+    if (Q >> 54) { sticky |= Q & 1u; Q >>= 1; e = 1; }
+    uint64_t M = Q >> 1;
+    const uint64_t g = Q & 1u;
+    M += g & (sticky | (M & 1u));
+    if (M >> 53) { M >>= 1; ++e; }
+    const int E = 53 + e - (33 - D.z) + aexp;      // value = Q * 2^(aexp - 33 + z)
+    return ((uint64_t)(E + 1023) << 52) | (M & ((1ull << 52) - 1));
+}
+
 // 128-bit N - R*R for R < 2^54, as (hi, lo) two's complement.
 SWA_HD void residual(uint64_t Nhi, uint64_t Nlo, uint64_t R, int64_t *rhi, uint64_t *rlo)
 {
@@ -256,11 +298,15 @@ SWA_HD void residual(uint64_t Nhi, uint64_t Nlo, uint64_t R, int64_t *rhi, uint6
 // Error budget: the seed R0 = fx * rsqrt(fx) * 2^26 has relative error below
 // 2^-21 (24-bit truncation of Mx, rsqrtf within 2 ulp, two float roundings),
 // so |R0 - sqrt(N)| < 2^32.  A correction R += (N - R^2) / (2R), with the
-// quotient formed in FP32 from the exact residual, leaves |R1 - sqrt(N)| <
-// 2^12 (2^11 from the quotient's 2^-21 relative error, 2^11 from Newton's
-// quadratic term), and a second one leaves |R2 - sqrt(N)| < 1.01 including
-// the truncation to an integer, so R2 is within -1..+2 of floor(sqrt(N)):
-// two exact steps each way (updating the remainder arithmetically) reach it.
+// quotient formed in FP32 from the exact residual (relative error below
+// 2^-20 with the truncation of the residual to its top 64 bits), leaves
+// |R1 - sqrt(N)| < 2^12 (2^11 from the quotient's error, 2^11 from Newton's
+// quadratic term, 1 from truncating the step).  The second correction's
+// quotient error is then below 2^12 * 2^-20 = 2^-8 and its quadratic term
+// below 2^-28; rounding the step to the nearest integer adds at most 1/2, so
+// |R2 - sqrt(N)| < 0.51.  Hence N - R2^2 lies within (2 sqrt(N) + 1) * 0.51
+// < 2^54 of zero: its low 64 bits, read as a signed integer, are its value,
+// and the nearest integer to sqrt(N) is R2 - 1, R2 or R2 + 1.
 SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
 {
     const int L = 64 - clz64(sig);
@@ -282,21 +328,11 @@ SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
         // (rh:rl) >> 32 fits int64 (|N - R^2| < 2^95)
         const int64_t top = (int64_t)(((uint64_t)rh << 32) | (rl >> 32));
         const float dlt = i64_to_float_trunc(top) * y * 32.0f;   // * 2^32 / 2^27
-        R = (uint64_t)((int64_t)R + float_to_i64_trunc(dlt));
+        R = (uint64_t)((int64_t)R + (it ? float_to_i64_rn(dlt) : float_to_i64_trunc(dlt)));
     }
-    // Exact floor: 0 <= rem = N - R^2 <= 2R.  rem is within (-2^57, 2^57).
-    int64_t rh;
-    uint64_t rl;
-    residual(Nhi, Nlo, R, &rh, &rl);
-    int64_t rem = (int64_t)rl;                     // rh is its sign extension
-#pragma unroll
-    for (int it = 0; it < 2; ++it)
-        if (rem < 0) { --R; rem += (int64_t)(2 * R + 1); }
-#pragma unroll
-    for (int it = 0; it < 2; ++it)
-        if (rem > (int64_t)(2 * R)) { rem -= (int64_t)(2 * R + 1); ++R; }
-    // Round to nearest: up iff rem > R.
-    R += rem > (int64_t)R ? 1u : 0u;
+    const int64_t rem = (int64_t)(Nlo - R * R);    // N - R^2, |.| < 2^54
+    if (rem > (int64_t)R) ++R;
+    else if (rem <= -(int64_t)R) --R;
     int e = E / 2 - 26;
     if (R >> 53) { R >>= 1; ++e; }
     return Fp{R, e};
@@ -335,7 +371,7 @@ SWA_HD double std_rn(uint64_t n, uint64_t sw, uint64_t qw, const Divisor &D)
     if ((d_hi | d_lo) == 0) return 0.0;
     const Fp d = round_u128(d_hi, d_lo);
     const Fp s = sqrt_rn(d.sig, d.exp);
-    return bits_to_double(div_rn(s.sig, s.exp, D));
+    return bits_to_double(div_rn53(s.sig, s.exp, D));
 }
 
 // std_rn for windows whose products n*qw and sw*sw both stay below 2^64
@@ -347,7 +383,7 @@ SWA_HD double std_rn64(uint64_t n, uint64_t sw, uint64_t qw, const Divisor &D)
     if (d == 0) return 0.0;
     const Fp r = round_u64(d);
     const Fp s = sqrt_rn(r.sig, r.exp);
-    return bits_to_double(div_rn(s.sig, s.exp, D));
+    return bits_to_double(div_rn53(s.sig, s.exp, D));
 }
 
 }  // namespace rn

@@ -15,12 +15,16 @@ import oracle
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.fixture(scope="module")
-def rn():
-    out = os.path.join(tempfile.mkdtemp(), "exact_rn_host.so")
+def build_rn(seed_ulps=None):
+    """The helpers built for the host; seed_ulps pushes the square root's
+    reciprocal-square-root seed by that many ulp (the device's rsqrtf is
+    within 2 ulp)."""
+    tag = "" if seed_ulps is None else "_%+d" % seed_ulps
+    out = os.path.join(tempfile.mkdtemp(), "exact_rn_host%s.so" % tag)
+    extra = [] if seed_ulps is None else ["-DSWA_RSQRT_TEST_ULPS=(%d)" % seed_ulps]
     subprocess.check_call([
         "g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-        "-I", os.path.join(ROOT, "paper_2410_16291_gb300", "csrc"),
+        *extra, "-I", os.path.join(ROOT, "paper_2410_16291_gb300", "csrc"),
         os.path.join(ROOT, "tests", "exact_rn_host.cpp"), "-o", out])
     L = ctypes.CDLL(out)
     vp = ctypes.c_void_p
@@ -33,6 +37,11 @@ def rn():
     L.rn_div.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
     L.rn_div.restype = ctypes.c_double
     return L
+
+
+@pytest.fixture(scope="module")
+def rn():
+    return build_rn()
 
 
 def run_bulk(rn, n, sw, qw):
@@ -142,3 +151,47 @@ def test_std_64bit_variant_equals_128bit_path(rn, vmax):
     np.testing.assert_array_equal(s64, s128)
     _, want = oracle.stats_bulk(n, sw, qw)
     np.testing.assert_array_equal(s64, want)
+
+
+def near_midpoints(count, seed):
+    """Doubles whose square root lies within 1/32 of a midpoint between two
+    doubles: sig * 2^52 close to (R + 1/2)^2 for a 53-bit R.  There the last
+    Newton step can stop on the wrong neighbour and the final step to the
+    nearest integer has to move it (with a seed 2-4 ulp off, dropping either
+    direction of that step fails on these inputs)."""
+    import random
+    from fractions import Fraction
+    r = random.Random(seed)
+    xs = []
+    while len(xs) < count:
+        R = r.randrange(2**52, 2**53)
+        Mx = round(Fraction((2 * R + 1) ** 2, 2**54))
+        if 2**52 <= Mx < 2**54 and abs(Mx * 2**52 - (R * R + R)) < 2**49:
+            xs.append(math.ldexp(float(Mx), r.randrange(-40, 40) * 2 - 52))
+    return xs
+
+
+@pytest.mark.parametrize("ulps", [-4, -2, 2, 4])
+def test_sqrt_and_std_with_a_perturbed_seed(ulps):
+    """The square root stays correctly rounded, and std bit-exact, when the
+    reciprocal-square-root seed is off by 2 or 4 ulp either way (the device's
+    rsqrtf is within 2): the Newton corrections and the final step to the
+    nearest integer absorb it, also on inputs next to rounding midpoints."""
+    L = build_rn(ulps)
+    for x in near_midpoints(20000, 7):
+        assert L.rn_sqrt(x) == math.sqrt(x), x
+    rng = np.random.default_rng(100 + ulps)
+    xs = list(rng.random(20000) * 2.0 ** rng.integers(-60, 120, 20000))
+    xs += [float(k * k) for k in range(1, 3000)] + [float(k * k + 1) for k in range(1, 3000)]
+    xs += [float(k * k - 1) for k in range(2, 3000)]
+    xs += [2.0 ** e for e in range(-60, 120)] + [math.nextafter(2.0 ** e, 0) for e in range(-50, 100)]
+    xs += [math.nextafter(2.0 ** e, math.inf) for e in range(-50, 100)]
+    for x in xs:
+        if x > 0:
+            assert L.rn_sqrt(x) == math.sqrt(x), x
+    for nmax, vmax in [(1024 ** 2, 255), (2 ** 32 - 1, 65535), (64, 65535)]:
+        n, sw, qw = moments(rng, 20000, nmax, vmax)
+        m0, s0 = oracle.stats_bulk(n, sw, qw)
+        m1, s1 = run_bulk(L, n, sw, qw)
+        np.testing.assert_array_equal(m1, m0)
+        np.testing.assert_array_equal(s1, s0)

@@ -138,6 +138,35 @@ def test_constructed_D_edges(case):
     assert n * q - s * s == T
 
 
+def near_midpoint_D(count, seed, scale):
+    """Integers D = Mx * 4^scale whose square root lies within 1/32 of a
+    midpoint between two doubles (Mx * 2^52 close to (R + 1/2)^2 for a
+    53-bit R): where the square root's last Newton step can stop on the
+    wrong neighbour and the final step to the nearest has to move it."""
+    import random
+    from fractions import Fraction
+    r = random.Random(seed)
+    out = []
+    while len(out) < count:
+        R = r.randrange(2**52, 2**53)
+        Mx = round(Fraction((2 * R + 1) ** 2, 2**54))
+        if 2**52 <= Mx < 2**54 and abs(Mx * 2**52 - (R * R + R)) < 2**49:
+            out.append(Mx << (2 * scale))
+    return out
+
+
+@pytest.mark.parametrize("path,scale,lo,hi", [("int64", 0, 64, 100), ("int128", 4, 300, 340)])
+def test_sqrt_near_rounding_midpoints(path, scale, lo, hi):
+    """Windows whose D has a square root next to a rounding midpoint, through
+    the device's rsqrtf-seeded square root, bit for bit against the oracle."""
+    require_gpu()
+    for k, T in enumerate(near_midpoint_D(8, 61 + scale, scale)):
+        img = window_with_D(T, 65535, near(lo, hi), seed=k)
+        assert (img.size * 65535 < 2**32) == (path == "int64")
+        s, q = check_one_window(img)
+        assert img.size * q - s * s == T
+
+
 def two_valued(r, c, seed):
     """{0, 65535} pixels with the share of 65535 varying across the image."""
     rng = np.random.default_rng(seed)
