@@ -349,10 +349,11 @@ SWA_HD double fp_to_double(Fp f)
 }
 
 // mean and std of one window from its exact moments (n < 2^32, n >= 1).
+// The integer path serves areas n < 2^32 of pixels up to 65535, so
+// Sw < 2^48: converting it to double is exact and RN(Sw) = Sw.
 SWA_HD double mean_rn(uint64_t sw, const Divisor &D)
 {
-    const Fp a = round_u64(sw);
-    return bits_to_double(div_rn(a.sig, a.exp, D));
+    return bits_to_double(div_rn(sw, 0, D));
 }
 
 SWA_HD double std_rn(uint64_t n, uint64_t sw, uint64_t qw, const Divisor &D)
