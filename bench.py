@@ -36,7 +36,7 @@ METRIC = "SAT build Gpx/s + window outputs/s, % HBM peak; served p50/p99 vs plai
 # Thread instructions per window (sum, mean, std; 4 windows per thread) of
 # the window kernel, from ncu on the 12,288^2 stride-1 case
 # (profiles/window_stats_dense_12288x12288.md).
-INSTR_PER_WINDOW = 463.0
+INSTR_PER_WINDOW = 400.6
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e datasheet bandwidth, for context beside the measured peak
 

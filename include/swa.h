@@ -299,14 +299,19 @@ typedef struct {
 typedef struct {
     int32_t u8_tile_rows;       /* rows per uint8 tile: 32 or 64 (0: 64) */
     int32_t order;              /* 0: images in the given order; 1: largest first */
-    int32_t reserved[6];        /* must be 0 */
+    int32_t ticket_order;       /* each image's tiles: 0 along anti-diagonals; 1 row by row */
+    int32_t lookback;           /* 0: edge records (the default); 1: corner records */
+    int32_t warps;              /* warps per build block: 9 or 8 (0: 9) */
+    int32_t reserved[3];        /* must be 0 */
 } swa_batch_config;
 
 typedef struct swa_batch swa_batch;
 
 /* Validate the items, allocate tables and scratch for all of them, upload
  * the work descriptors (waits for that upload on `stream`).  cfg may be
- * NULL.  SWA_EINVAL / SWA_EOVERFLOW as for swa_build_sat and
+ * NULL (all defaults); its fields change speed only, never results: they
+ * are the autotuner's search space.  Out-of-range fields or non-zero
+ * reserved ones give SWA_EINVAL.  SWA_EINVAL / SWA_EOVERFLOW as for swa_build_sat and
  * swa_window_stats; SWA_ENOMEM if the plan does not fit. */
 swa_status swa_batch_create(const swa_batch_item *items, int32_t n,
                             const swa_batch_config *cfg, swa_stream stream,

@@ -63,7 +63,9 @@ struct BatchArgs {
     uint32_t diag;                    // each image's tiles in anti-diagonal order
 };
 
-constexpr int kBatchWarps = 9;
+// Warps per build block: 9 (as many as the SM's shared memory holds) or 8;
+// a configuration choice the autotuner may make.
+constexpr int kBatchWarpsMax = 9;
 // Shared memory per warp: the larger of the uint8 (64-row) and uint16 tile
 // routines, so warps working on different dtypes never overlap.
 constexpr int kBatchWarpBytes =
@@ -173,8 +175,8 @@ __global__ void __launch_bounds__(256) k_batch_windows(const BQuery *__restrict_
 }
 
 // Builds: one persistent launch over the tiles of every image.
-template <int TH8>
-__global__ void __launch_bounds__(kBatchWarps * 32, 1) k_batch(const __grid_constant__ BatchArgs a)
+template <int TH8, int W>
+__global__ void __launch_bounds__(W * 32, 1) k_batch(const __grid_constant__ BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -184,8 +186,11 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_batch(const __grid_cons
     WarpRes w = warp_res<uint8_t, TH8>(smem_raw, kBatchWarpBytes);
     // A warp's tickets only increase, so it caches the ticket range of its
     // current image and searches only past it.
+    // The image's tensor maps (written by the host before the launch) are
+    // acquired for the tensor-map proxy once per image the warp works on.
     int k = 0;
     uint32_t lo = a.imgs[0].tile_base, hi = lo + a.imgs[0].ntiles;
+    bool acquired = false;
     for (;;) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(a.ticket, 1u);
@@ -195,11 +200,15 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) k_batch(const __grid_cons
             k += find_base(a.nimg - k, t, [&](int i) { return a.imgs[k + i].tile_base; });
             lo = a.imgs[k].tile_base;
             hi = lo + a.imgs[k].ntiles;
+            acquired = false;
         }
         const BImg &im = a.imgs[k];
         const uint32_t tl = a.diag ? diag_tile(t - lo, im.nby, im.nsx) : t - lo;
-        tensormap_acquire(&im.tmS);
-        tensormap_acquire(&im.tmQ);
+        if (!acquired) {
+            tensormap_acquire(&im.tmS);
+            tensormap_acquire(&im.tmQ);
+            acquired = true;
+        }
         bool ok;
         if (im.dtype == SWA_U8)
             ok = im.vec ? batch_tile<uint8_t, true, TH8>(im, tl, a.err, w)
@@ -224,7 +233,7 @@ using namespace swa;
 struct swa_batch {
     uint64_t tag;
     int device;
-    int32_t nimg, nq, th8;
+    int32_t nimg, nq, th8, warps;
     uint32_t total_tiles, total_items;
     char *mem;                        // one allocation: descriptors, state, scratch, tables
     int64_t mem_bytes;
@@ -252,6 +261,15 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
         set_error("u8_tile_rows must be 32 or 64");
         return SWA_EINVAL;
     }
+    const int warps = cfg && cfg->warps ? cfg->warps : kBatchWarpsMax;
+    if (cfg && (cfg->order < 0 || cfg->order > 1 || cfg->ticket_order < 0 ||
+                cfg->ticket_order > 1 || cfg->lookback < 0 || cfg->lookback > 1 ||
+                (warps != 9 && warps != 8) || cfg->reserved[0] || cfg->reserved[1] ||
+                cfg->reserved[2])) {
+        set_error("bad batch configuration");
+        return SWA_EINVAL;
+    }
+    const bool corner_all = cfg && cfg->lookback == 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // Image order: as given, or largest first.
     std::vector<int32_t> order(n);
@@ -322,6 +340,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     b->nimg = n;
     b->nq = (int32_t)nq;
     b->th8 = th8;
+    b->warps = warps;
     b->table_off.resize(n);
     b->ld.resize(n);
     b->rows.resize(n);
@@ -346,7 +365,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
         m.vec = ((uintptr_t)it.image % vb == 0) && (it.pitch_bytes % vb == 0);
         m.nby = (it.rows + th - 1) / th;
         m.nsx = (it.cols + kSliceCols - 1) / kSliceCols;
-        m.corner_mode = corner_mode_for(m.nsx, it.dtype) ? 1 : 0;
+        m.corner_mode = (corner_all || corner_mode_for(m.nsx, it.dtype)) ? 1 : 0;
         m.ld = (it.cols + kLdAlign - 1) / kLdAlign * kLdAlign;
         m.ntiles = (uint32_t)(m.nby * m.nsx);
         m.tile_base = tile_base;
@@ -455,7 +474,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     a.total_items = item_base;
     a.ticket = reinterpret_cast<uint32_t *>(base + off_ticket);
     a.err = reinterpret_cast<uint32_t *>(base + off_err);
-    a.diag = ticket_order_diag() ? 1u : 0u;
+    a.diag = (ticket_order_diag() && !(cfg && cfg->ticket_order == 1)) ? 1u : 0u;
     *out = b;
     return SWA_OK;
 }
@@ -469,8 +488,10 @@ swa_status swa_batch_run(swa_batch *b, swa_stream stream)
         set_error("cudaMemsetAsync: %s", cudaGetErrorString(e));
         return SWA_ECUDA;
     }
-    const size_t smem = 1024 + (size_t)kBatchWarps * kBatchWarpBytes;
-    auto kern = b->th8 == 64 ? k_batch<64> : k_batch<32>;
+    const int W = b->warps;
+    const size_t smem = 1024 + (size_t)W * kBatchWarpBytes;
+    auto kern = W == 9 ? (b->th8 == 64 ? k_batch<64, 9> : k_batch<32, 9>)
+                       : (b->th8 == 64 ? k_batch<64, 8> : k_batch<32, 8>);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess) {
         set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
@@ -478,12 +499,11 @@ swa_status swa_batch_run(swa_batch *b, swa_stream stream)
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    int64_t blocks = std::min<int64_t>(sms, ((int64_t)b->total_tiles + kBatchWarps - 1) /
-                                                kBatchWarps);
+    int64_t blocks = std::min<int64_t>(sms, ((int64_t)b->total_tiles + W - 1) / W);
     if (blocks < 1) blocks = 1;
     {
         LaunchScope ls("batch_build", s);
-        kern<<<(unsigned)blocks, kBatchWarps * 32, smem, s>>>(b->args);
+        kern<<<(unsigned)blocks, W * 32, smem, s>>>(b->args);
     }
     if (b->total_items) {
         LaunchScope ls("batch_windows", s);

@@ -1,27 +1,38 @@
 """Autotuner for the batched engine's configuration.
 
-The batched launch has two knobs (``swa_batch_config``): the height of a
-uint8 SAT tile (32 or 64 rows: shorter tiles mean more tiles and look-back
-records, taller ones more shared memory per warp) and the image order (as
-given, or largest first, which lets small images fill the tail).  ``tune``
-times every candidate on a deterministic sample of the batch's images with
-CUDA events and keeps the fastest.  Results are cached in a JSON file keyed
-by the device and a coarse description of the batch, so a later batch of
-the same kind skips the search.  The cache file is ``$SWA_TUNE_CACHE`` if
-set, else ``~/.cache/paper_2410_16291_gb300/tune.json``.
+The batched launch's knobs (``swa_batch_config``) change speed, never
+results:
+
+- the height of a uint8 SAT tile (64 or 32 rows: shorter tiles mean more
+  tiles and look-back records, taller ones more shared memory per warp);
+- the image order (as given, or largest first, which lets small images fill
+  the tail);
+- the order of each image's tiles in the work queue (along anti-diagonals,
+  or row by row);
+- the look-back mode (edge records, or corner records from the tile above
+  and to the left);
+- the warps per build block (9, as many as shared memory holds, or 8).
+
+``tune`` times every combination (32 candidates) on a deterministic sample
+of the batch's images with CUDA events and keeps the fastest.  Results are
+cached in a JSON file keyed by the device and a coarse description of the
+batch, so a later batch of the same kind skips the search.  The cache file
+is ``$SWA_TUNE_CACHE`` if set, else
+``~/.cache/paper_2410_16291_gb300/tune.json``.
 """
 from __future__ import annotations
 
+import itertools
 import json
 import math
 import os
 
-CANDIDATES = (
-    {"u8_tile_rows": 64, "order": 0},
-    {"u8_tile_rows": 64, "order": 1},
-    {"u8_tile_rows": 32, "order": 0},
-    {"u8_tile_rows": 32, "order": 1},
-)
+AXES = (("u8_tile_rows", (64, 32)), ("order", (0, 1)), ("ticket_order", (0, 1)),
+        ("lookback", (0, 1)), ("warps", (9, 8)))
+# Every combination, the library's defaults first.
+CANDIDATES = tuple(dict(zip([k for k, _ in AXES], v))
+                   for v in itertools.product(*[vals for _, vals in AXES]))
+KEY_VERSION = 2
 
 
 def cache_path() -> str:
@@ -58,8 +69,9 @@ def batch_key(device: str, shapes, dtypes) -> str:
     n = len(shapes)
     px = sum(r * c for r, c in shapes) / max(1, n)
     u16 = sum(1 for d in dtypes if d == "u16") / max(1, n)
-    return "%s|n%d|px%d|u16q%d" % (device, 1 << max(0, int(math.log2(max(1, n)))),
-                                   int(math.log2(max(1.0, px))), int(round(u16 * 4)))
+    return "v%d|%s|n%d|px%d|u16q%d" % (KEY_VERSION, device,
+                                       1 << max(0, int(math.log2(max(1, n)))),
+                                       int(math.log2(max(1.0, px))), int(round(u16 * 4)))
 
 
 def choose(times: dict) -> dict:

@@ -114,3 +114,16 @@ def test_test_hooks_validate(L):
     assert L.swa_set_test_hooks(swa.SWA_HOOK_CORNER_MODE | swa.SWA_HOOK_ROW_ORDER) == swa.SWA_OK
     assert L.swa_set_test_hooks(0) == swa.SWA_OK
     assert L.swa_set_test_hooks(16) == swa.SWA_EINVAL
+
+
+def test_batch_config_checked_on_the_host(L):
+    """A batch configuration out of range is refused before any device work."""
+    item = swa.swa_batch_item(ctypes.c_void_p(0x1000), 4, 4, 4, swa.SWA_U8, 0, None)
+    items = (swa.swa_batch_item * 1)(item)
+    h = ctypes.c_void_p()
+    for bad in [dict(u8_tile_rows=48), dict(order=2), dict(ticket_order=-1), dict(lookback=2),
+                dict(warps=7), dict(reserved=(ctypes.c_int32 * 3)(0, 1, 0))]:
+        cfg = swa.swa_batch_config(**bad)
+        assert L.swa_batch_create(items, 1, ctypes.byref(cfg), None, ctypes.byref(h)) == \
+            swa.SWA_EINVAL, bad
+        assert h.value is None

@@ -53,14 +53,22 @@ def check_batch(batch, imgs, wins):
             np.testing.assert_array_equal(f64(got["std"]), want["std"])
 
 
-@pytest.mark.parametrize("tile_rows,order", [(64, 0), (32, 1)])
-def test_batch_bitexact_and_repeatable(tile_rows, order):
+@pytest.mark.parametrize("cfg", [
+    dict(u8_tile_rows=64, order=0), dict(u8_tile_rows=32, order=1),
+    dict(u8_tile_rows=64, order=0, ticket_order=1, lookback=1, warps=8),
+    dict(u8_tile_rows=32, order=0, ticket_order=1, lookback=0, warps=9),
+    dict(u8_tile_rows=64, order=1, ticket_order=0, lookback=1, warps=9),
+    dict(u8_tile_rows=32, order=1, ticket_order=0, lookback=0, warps=8)],
+    ids=lambda c: "-".join("%s%d" % (k[:2], v) for k, v in c.items()))
+def test_batch_bitexact_and_repeatable(cfg):
+    """Every configuration the autotuner may pick gives the same, exact
+    tables and outputs."""
     require_gpu()
     import torch
     from paper_2410_16291_gb300 import build
     build.build()
     imgs, devs, wins = make_case()
-    b = swa.Batch(devs, wins, u8_tile_rows=tile_rows, order=order)
+    b = swa.Batch(devs, wins, **cfg)
     b.run()
     b.sync()
     check_batch(b, imgs, wins)
