@@ -7,10 +7,8 @@
 //     row by row), each processed by the single-pass tile routine with
 //     decoupled look-back inside its image.
 //  2. k_batch_windows: one launch evaluates every query of every image; a
-//     block covers 1024 consecutive windows of one query's output grid in
-//     row-major order (across output rows, so narrow grids leave no thread
-//     idle) and finds its query by binary search over the queries' block
-//     offsets.
+//     block covers 1024 consecutive windows of one output row of one query
+//     and finds its query by binary search over the queries' block offsets.
 //
 // The windows run in a launch of their own because the build's tiles need
 // 25 KB of shared memory per warp (9 warps per SM), while the window
@@ -52,8 +50,7 @@ struct BQuery {
     rn::Divisor div;
     int32_t img, int_rn;
     int32_t d64;                      // std from a 64-bit D (n * max pixel < 2^32)
-    uint32_t cm;                      // min(2^32 - 1, floor(2^32 / C)): row of a flat index
-    uint32_t nwin;                    // R * C (below 2^32)
+    int64_t nbx;                      // blocks per output row
     uint32_t item_base, nitems;       // first block, blocks
 };
 
@@ -124,10 +121,7 @@ constexpr int kBWinPerThread = 4;
 constexpr int kBWinPerBlock = 256 * kBWinPerThread;
 
 // Queries of all images: block -> query by binary search, then 1024
-// consecutive windows of the query's output grid in row-major order (thread
-// t: flat indices t, t+256, t+512, t+768 of the block's range).  The output
-// row of flat index f is floor(f / C): the estimate floor(f * cm / 2^32) is
-// that or one less for every f < 2^32, so one step corrects it.
+// consecutive windows of one output row (thread t: t, t+256, t+512, t+768).
 __global__ void __launch_bounds__(256) k_batch_windows(const BQuery *__restrict__ qs, int32_t nq,
                                                        const BImg *__restrict__ imgs)
 {
@@ -135,23 +129,22 @@ __global__ void __launch_bounds__(256) k_batch_windows(const BQuery *__restrict_
     const int qi = find_base(nq, bid, [&](int i) { return qs[i].item_base; });
     const BQuery &q = qs[qi];
     const BImg &im = imgs[q.img];
-    const uint32_t f0 = (bid - q.item_base) * (uint32_t)kBWinPerBlock + threadIdx.x;
+    const uint32_t blk = bid - q.item_base;
+    const uint32_t nbx = (uint32_t)q.nbx;
+    const uint32_t i = blk / nbx;
+    const int64_t jb = (int64_t)(blk - i * nbx) * kBWinPerBlock + threadIdx.x;
     const int64_t ld = im.ld;
-    const uint32_t C = (uint32_t)q.w.C;
+    const int64_t y0 = (int64_t)i * q.w.sy, y1 = y0 + q.w.wh - 1;
+    const bool top = y0 > 0;
+    const uint64_t *St = im.S + (y0 - 1) * ld, *Sb = im.S + y1 * ld;
+    const uint64_t *Qt = im.Q + (y0 - 1) * ld, *Qb = im.Q + y1 * ld;
     const uint32_t o = q.w.outputs;
+    const int64_t orow = (int64_t)i * q.w.out_ld;
 #pragma unroll
     for (int m = 0; m < kBWinPerThread; ++m) {
-        const uint32_t f = f0 + 256u * (uint32_t)m;
-        if (f >= q.nwin) break;
-        uint32_t i = __umulhi(f, q.cm);
-        uint32_t j = f - i * C;
-        if (j >= C) { ++i; j -= C; }
-        const int64_t y0 = (int64_t)i * q.w.sy, y1 = y0 + q.w.wh - 1;
-        const bool top = y0 > 0;
-        const uint64_t *St = im.S + (y0 - 1) * ld, *Sb = im.S + y1 * ld;
-        const uint64_t *Qt = im.Q + (y0 - 1) * ld, *Qb = im.Q + y1 * ld;
-        const int64_t orow = (int64_t)i * q.w.out_ld;
-        const int64_t x0 = (int64_t)j * q.w.sx, x1 = x0 + q.w.ww - 1;
+        const int64_t j = jb + 256 * m;
+        if (j >= q.w.C) break;
+        const int64_t x0 = j * q.w.sx, x1 = x0 + q.w.ww - 1;
         const bool left = x0 > 0;
         uint64_t sw = __ldg(Sb + x1);
         if (top) sw -= __ldg(St + x1);
@@ -319,11 +312,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
                 set_error("batch item %d window %d: out_ld < %lld", i, k, (long long)C);
                 return SWA_EINVAL;
             }
-            if (R * C >= 0xffffffffLL) {
-                set_error("batch item %d window %d: more than 2^32 - 1 windows", i, k);
-                return SWA_EINVAL;
-            }
-            items_w += (R * C + kBWinPerBlock - 1) / kBWinPerBlock;
+            items_w += R * ((C + kBWinPerBlock - 1) / kBWinPerBlock);
             ++nq;
         }
     }
@@ -455,10 +444,9 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
             q.d64 = q.int_rn && q.n * (it.dtype == SWA_U8 ? 255ull : 65535ull) < (1ull << 32);
             q.div = rn::make_divisor(q.int_rn ? (uint32_t)q.n : 1u);
             q.img = pos;
-            q.nwin = (uint32_t)(q.w.R * q.w.C);
-            q.cm = (uint32_t)std::min<uint64_t>(0xffffffffull, (1ull << 32) / (uint64_t)q.w.C);
+            q.nbx = (q.w.C + kBWinPerBlock - 1) / kBWinPerBlock;
             q.item_base = item_base;
-            q.nitems = (q.nwin + kBWinPerBlock - 1) / kBWinPerBlock;
+            q.nitems = (uint32_t)(q.w.R * q.nbx);
             item_base += q.nitems;
         }
     }
