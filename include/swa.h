@@ -69,9 +69,21 @@ enum {
     SWA_WITH_SQ = 1u,   /* also build Q, the table of squared pixels (needed for std) */
     SWA_TWOPASS = 2u,   /* read the image twice (reduce, then scan) instead of the
                            single pass with decoupled look-back */
-    SWA_COUNT = 4u      /* reported by swa_sat_info for count tables
+    SWA_COUNT = 4u,     /* reported by swa_sat_info for count tables
                            (swa_build_count_sat); not a build flag */
+    SWA_LATTICE_SHIFT = 8,      /* flag bits 8..15: corner lattice stride */
+    SWA_LATTICE_MASK = 0xff00u
 };
+/* Build flag: also keep the corner lattice of stride s (8 <= s <= 255): the
+ * entries of S and Q at rows y and columns x where y + 1 and x + 1 are
+ * multiples of s, packed in their own small arrays (1/s^2 of the tables).
+ * Every corner of a window at strides (s, s) whose sides are multiples of s
+ * lies on that lattice (top-left pixel (s*i, s*j): corner rows s*i - 1 and
+ * s*i + wh - 1), so swa_window_stats* evaluates such queries from the
+ * lattice, reading dense rows instead of one scattered entry per 64-byte
+ * line; results are the same.  Needs SWA_WITH_SQ, not SWA_TWOPASS.  The
+ * paper's corner lookup (Section II-B) on a subsampled table. */
+#define SWA_LATTICE(s) ((uint32_t)(s) << SWA_LATTICE_SHIFT)
 
 /* Window output selection. */
 enum { SWA_OUT_SUM = 1u, SWA_OUT_MEAN = 2u, SWA_OUT_STD = 4u };
@@ -96,7 +108,7 @@ typedef struct {
  *                passed this call.
  *   pitch_bytes  distance between rows, >= cols * pixel size; for uint16 the
  *                base address and the pitch must be even (SWA_EINVAL otherwise).
- *   flags        SWA_WITH_SQ, SWA_TWOPASS.
+ *   flags        SWA_WITH_SQ, SWA_TWOPASS, SWA_LATTICE(s).
  *   stream       the build runs on it; the handle keeps it as its home stream.
  *   out          receives a new handle that owns S and Q (stream-ordered
  *                allocations on `stream`); set to NULL on error.
@@ -193,6 +205,14 @@ swa_status swa_window_stats_multi(const swa_sat *sat, const swa_window *windows,
  * stream order after the build. */
 swa_status swa_sat_data(const swa_sat *sat, const uint64_t **d_S,
                         const uint64_t **d_Q, int64_t *ld);
+
+/* Borrowed device views of the corner lattice (see SWA_LATTICE): lattice
+ * entry (a, b) of S is S[s*(a+1) - 1][s*(b+1) - 1], for a < rows / s and
+ * b < cols / s, at d_LS[a * ld + b] (d_LQ likewise for Q).  A handle built
+ * without a lattice (or too small to hold one) reports stride 0 and NULL
+ * views.  Any output pointer may be NULL.  Valid until swa_free. */
+swa_status swa_sat_lattice(const swa_sat *sat, const uint64_t **d_LS, const uint64_t **d_LQ,
+                           int64_t *rows, int64_t *cols, int64_t *ld, int32_t *stride);
 
 /* Shape, dtype and flags of a handle. */
 swa_status swa_sat_info(const swa_sat *sat, int64_t *rows, int64_t *cols,

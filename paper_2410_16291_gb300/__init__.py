@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libswa.so")
 SWA_U8, SWA_U16 = 1, 2
 SWA_OK, SWA_EINVAL, SWA_EOVERFLOW, SWA_ENOMEM, SWA_ECUDA, SWA_ETIMEOUT = range(6)
 SWA_WITH_SQ, SWA_TWOPASS, SWA_COUNT = 1, 2, 4
+SWA_LATTICE_SHIFT = 8
 SWA_OUT_SUM, SWA_OUT_MEAN, SWA_OUT_STD = 1, 2, 4
 SWA_MAX_WINDOWS = 64
 SWA_HOOK_STALL_TILE0 = 1
@@ -64,6 +65,8 @@ SIGNATURES = {
     "swa_window_stats": (ctypes.c_int, [_VP, _I64, _I64, _I64, _I64, _U32, _VP, _VP, _VP, _I64, _VP]),
     "swa_window_stats_multi": (ctypes.c_int, [_VP, _P(swa_window), _I32, _VP]),
     "swa_sat_data": (ctypes.c_int, [_VP, _P(_VP), _P(_VP), _P(_I64)]),
+    "swa_sat_lattice": (ctypes.c_int, [_VP, _P(_VP), _P(_VP), _P(_I64), _P(_I64), _P(_I64),
+                                       _P(_I32)]),
     "swa_sat_info": (ctypes.c_int, [_VP, _P(_I64), _P(_I64), _P(_I32), _P(_U32)]),
     "swa_sat_bytes": (ctypes.c_int, [_I64, _I64, ctypes.c_int, _U32, _P(_I64), _P(_I64)]),
     "swa_sync": (ctypes.c_int, [_VP]),
@@ -236,6 +239,19 @@ class SAT:
         return _view_u64(S.value, self.rows, self.cols, ld.value), (
             _view_u64(Q.value, self.rows, self.cols, ld.value) if Q.value else None)
 
+    def lattice(self):
+        """(stride, LS, LQ): the corner lattice of a build with ``lattice=s``
+        (int64 views, uint64 bit patterns; entry (a, b) is the table entry at
+        row s*(a+1)-1, column s*(b+1)-1), or (0, None, None) without one."""
+        LS, LQ, r, c, ld, st = _VP(), _VP(), _I64(), _I64(), _I64(), _I32()
+        check(lib().swa_sat_lattice(self.handle, ctypes.byref(LS), ctypes.byref(LQ),
+                                    ctypes.byref(r), ctypes.byref(c), ctypes.byref(ld),
+                                    ctypes.byref(st)), "swa_sat_lattice")
+        if not st.value:
+            return 0, None, None
+        return (st.value, _view_u64(LS.value, r.value, c.value, ld.value),
+                _view_u64(LQ.value, r.value, c.value, ld.value))
+
     def sync(self):
         check(lib().swa_sync(self.handle), "swa_sync")
 
@@ -269,13 +285,16 @@ def _view_u64(ptr, rows, cols, ld):
     return torch.as_tensor(_Arr(), device="cuda")
 
 
-def build_sat(image, with_sq=True, twopass=False, stream=None) -> SAT:
+def build_sat(image, with_sq=True, twopass=False, stream=None, lattice=0) -> SAT:
     """Build S (and Q) of a 2-D uint8/uint16 CUDA tensor (row stride may exceed
-    its width)."""
+    its width).  ``lattice=s`` (8..255) also keeps the corner lattice of
+    stride s, which serves window queries at strides (s, s) whose sides are
+    multiples of s (see SWA_LATTICE in swa.h)."""
     assert image.is_cuda and image.dim() == 2 and image.stride(1) == 1
     rows, cols = image.shape
     h = _VP()
-    flags = (SWA_WITH_SQ if with_sq else 0) | (SWA_TWOPASS if twopass else 0)
+    flags = (SWA_WITH_SQ if with_sq else 0) | (SWA_TWOPASS if twopass else 0) | (
+        int(lattice) << SWA_LATTICE_SHIFT)
     check(lib().swa_build_sat(image.data_ptr(), rows, cols, image.stride(0) * image.element_size(),
                               _dtype_code(image), flags, _stream_ptr(stream), ctypes.byref(h)),
           "swa_build_sat")

@@ -293,7 +293,7 @@ k_scan(const char *__restrict__ img, int64_t pitch, int64_t rows, int64_t cols,
     __syncwarp();
 }
 
-template <typename T, bool WQ, bool VEC, int TH, int W, bool THR>
+template <typename T, bool WQ, bool VEC, int TH, int W, bool THR, bool LAT>
 __global__ void __launch_bounds__(W * 32, 1)
 k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
           const __grid_constant__ CUtensorMap tmQ)
@@ -320,6 +320,10 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
     c.tmQ = &tmQ;
     c.thr = a.thr;
     c.corner_mode = a.corner_mode != 0;
+    c.lat_s = a.lat_s;
+    c.lat_q = a.lat_q;
+    c.lat_ld = a.lat_ld;
+    c.lat_stride = a.lat_stride;
     const int64_t ntiles = a.nby * a.nsx;
     for (;;) {
         uint32_t t = 0;
@@ -328,7 +332,7 @@ k_onepass(OnePass a, const __grid_constant__ CUtensorMap tmS,
         if ((int64_t)t >= ntiles || *(volatile uint32_t *)a.err) break;
         if (t == 0 && a.stall_tile0) continue;
         const uint32_t tile = a.diag ? diag_tile(t, a.nby, a.nsx) : t;
-        if (!onepass_tile<T, WQ, VEC, TH, THR>(c, tile, a.err, w)) break;
+        if (!onepass_tile<T, WQ, VEC, TH, THR, LAT>(c, tile, a.err, w)) break;
     }
     cp_async_wait_all();
     if (lane == 0) bulk_wait_all();
@@ -417,7 +421,7 @@ template <typename T, bool WQ> constexpr int onepass_warps()
                : 16;
 }
 
-template <typename T, bool WQ, bool VEC, bool THR = false>
+template <typename T, bool WQ, bool VEC, bool THR = false, bool LAT = false>
 swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint64_t *Q,
                           char *scratch, uint32_t *err, cudaStream_t st)
 {
@@ -445,6 +449,10 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
     a.diag = ticket_order_diag() ? 1u : 0u;
     a.thr = p.thr;
     a.corner_mode = p.corner ? 1u : 0u;
+    a.lat_s = p.lat_S;
+    a.lat_q = p.lat_Q;
+    a.lat_ld = p.lat_ld;
+    a.lat_stride = p.lat_s;
     CUtensorMap tmS, tmQ;
     if (!table_tensor_map(&tmS, S, p.rows, p.ld) ||
         !table_tensor_map(&tmQ, WQ ? Q : S, p.rows, p.ld)) {
@@ -453,7 +461,7 @@ swa_status launch_onepass(const BuildPlan &p, const char *img, uint64_t *S, uint
         return SWA_ECUDA;
     }
     const size_t smem = 1024 + (size_t)W * onepass_warp_bytes<T, TH, WQ>();
-    auto kern = k_onepass<T, WQ, VEC, TH, W, THR>;
+    auto kern = k_onepass<T, WQ, VEC, TH, W, THR, LAT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return launch_error("cudaFuncSetAttribute", e);
@@ -485,6 +493,10 @@ swa_status dispatch_onepass(const BuildPlan &p, const char *img, uint64_t *S, ui
     if (p.count)        // indicator table: S only
         return p.vec ? launch_onepass<T, false, true, true>(p, img, S, Q, scratch, err, st)
                      : launch_onepass<T, false, false, true>(p, img, S, Q, scratch, err, st);
+    if (p.with_q && p.lat_s && p.lat_S)  // S, Q and their corner lattice
+        return p.vec ? launch_onepass<T, true, true, false, true>(p, img, S, Q, scratch, err, st)
+                     : launch_onepass<T, true, false, false, true>(p, img, S, Q, scratch, err,
+                                                                   st);
     if (p.with_q)
         return p.vec ? launch_onepass<T, true, true>(p, img, S, Q, scratch, err, st)
                      : launch_onepass<T, true, false>(p, img, S, Q, scratch, err, st);
@@ -512,6 +524,14 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
     const int64_t vbytes = dtype == SWA_U8 ? 8 : 16;
     p.vec = ((uintptr_t)image % vbytes == 0) && (pitch % vbytes == 0);
     p.count = (flags & kCountPlan) != 0;
+    // Corner lattice stride (flag bits 8..15; single pass with Q only).  The
+    // caller supplies the lattice arrays (lat_S, lat_Q, lat_ld).
+    p.lat_s = (!p.twopass && !p.count && p.with_q) ? (int)((flags >> SWA_LATTICE_SHIFT) & 0xffu)
+                                                   : 0;
+    p.lat_rows = p.lat_s ? rows / p.lat_s : 0;
+    p.lat_cols = p.lat_s ? cols / p.lat_s : 0;
+    if (!p.lat_rows || !p.lat_cols) p.lat_s = 0;
+    p.lat_ld = p.lat_s ? (p.lat_cols + kLdAlign - 1) / kLdAlign * kLdAlign : 0;
     p.th = p.twopass ? kTH
                      : (dtype == SWA_U8 ? onepass_rows<uint8_t>() : onepass_rows<uint16_t>());
     p.nby = (rows + p.th - 1) / p.th;

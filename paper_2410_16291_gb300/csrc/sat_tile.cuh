@@ -304,6 +304,12 @@ struct OnePass {
     uint32_t diag;                    // tickets along anti-diagonals (diag_tile)
     uint32_t thr;                     // count tables: pixels > thr count 1, others 0
     uint32_t corner_mode;             // K from corner records (else edge mode)
+    // Corner lattice (builds with a lattice stride st): the entries of S and Q
+    // at rows y and columns x with y + 1 and x + 1 multiples of st, as
+    // lat_s[(y + 1) / st - 1][(x + 1) / st - 1] (leading dimension lat_ld).
+    uint64_t *lat_s, *lat_q;
+    int64_t lat_ld;
+    int32_t lat_stride;
 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
@@ -409,6 +415,9 @@ struct TileCtx {
     const CUtensorMap *tmS, *tmQ;
     uint32_t thr;                     // with THR: the threshold of the count table
     bool corner_mode;                 // K from corner records (else edge mode)
+    uint64_t *lat_s, *lat_q;          // with LAT: the corner lattice (see OnePass)
+    int64_t lat_ld;
+    int32_t lat_stride;               // 8..255
 };
 
 // Per-warp resources of the tile routine (the same for every pixel type, so
@@ -646,9 +655,12 @@ __device__ __forceinline__ bool lookback_tile(const TileCtx &a, uint32_t t, int6
 }
 
 // Process tile t of one image (single pass): stage, reduce, publish, look
-// back, publish, scan, write.  Returns false if a wait gave up (the error
-// word is then set).
-template <typename T, bool WQ, bool VEC, int TH, bool THR = false>
+// back, publish, scan, write.  With LAT the scan also writes the tile's
+// entries of the corner lattice (rows and columns one below a multiple of
+// the lattice stride, which is at least 8, so a lane's 8 columns hold at most
+// one lattice column).  Returns false if a wait gave up (the error word is
+// then set).
+template <typename T, bool WQ, bool VEC, int TH, bool THR = false, bool LAT = false>
 __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint32_t *err,
                                              WarpRes &w)
 {
@@ -794,6 +806,41 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     if (!lookback_tile<WQ, TH>(a, t, b, s, cs, cq, rs_s, rs_q, err, vs, vq, lr_s, lr_q))
         return false;
 
+    // Corner lattice: the tile's first lattice row and lattice row index, the
+    // lane's lattice column (lat_k: its position among the lane's 8 columns,
+    // -1 if none) and lattice column index.
+    int64_t lat_y = 0, lat_i = 0, lat_j = 0;
+    int lat_k = -1;
+    if (LAT) {
+        const int64_t st = a.lat_stride;
+        lat_y = (y0 + st) / st * st - 1;              // first y >= y0 with st | y + 1
+        lat_i = (lat_y + 1) / st - 1;
+        const int64_t xn = (x + st) / st * st - 1;    // first column >= x likewise
+        if (xn < x + kPxPerLane && xn < a.cols) {
+            lat_k = (int)(xn - x);
+            lat_j = (xn + 1) / st - 1;
+        }
+    }
+    // Writes the lane's lattice entry of row y (values as emit_row forms them).
+    auto lat_row = [&](int64_t y, uint64_t base_s, const uint32_t *lp, uint64_t base_q,
+                       const QA *lq) {
+        if (!LAT || y != lat_y) return;
+        if (lat_k >= 0) {
+            uint64_t vS = 0, vQ = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k == lat_k) {
+                    vS = base_s + vs[k] + lp[k];
+                    if (WQ) vQ = base_q + vq[k] + (uint64_t)lq[k];
+                }
+            const int64_t off = lat_i * a.lat_ld + lat_j;
+            a.lat_s[off] = vS;
+            if (WQ) a.lat_q[off] = vQ;
+        }
+        lat_y += a.lat_stride;
+        ++lat_i;
+    };
+
     // Rows go in pairs: the two rows' prefix and warp-scan chains are
     // independent, which gives the scheduler two chains to interleave.
     uint32_t cp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -848,9 +895,12 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
             }
             emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_as, vs, la, base_aq, vq, qa, a.tmS,
                              a.tmQ, c1, (int)(y0 + r), w.pol);
-            if (r + 1 < nr)
+            lat_row(y0 + r, base_as, la, base_aq, qa);
+            if (r + 1 < nr) {
                 emit_row<WQ, QA>(w.ring, w.slot, w.sw, base_bs, vs, lb, base_bq, vq, qb, a.tmS, a.tmQ,
                                  c1, (int)(y0 + r + 1), w.pol);
+                lat_row(y0 + r + 1, base_bs, lb, base_bq, qb);
+            }
         }
     }
     __syncwarp();     // the tile buffer is reused by the next ticket

@@ -95,12 +95,53 @@ swa_status check_window(const Handle *h, const swa_window &w, WinDesc *d)
     }
     d->out_ld = w.out_ld;
     d->row0 = 0;
+    d->area = 0;
     d->outputs = o;
     d->vmax = (h->flags & SWA_COUNT) ? 1u : h->dtype == SWA_U8 ? 255u : 65535u;
     d->sum = w.sum;
     d->mean = w.mean;
     d->std = w.std;
     return SWA_OK;
+}
+
+// A query whose every corner lies on the handle's corner lattice (strides
+// (s, s), sides multiples of s, windows from table row 0), rewritten as the
+// stride-1 query of side wh/s x ww/s on the lattice with the true area: the
+// corner rows s*i - 1 and s*i + wh - 1 are lattice rows i - 1 and
+// i + wh/s - 1 (row -1 reading as 0, like the table's), and the lattice's
+// output grid, lat_rows - wh/s + 1 rows, is the query's
+// floor((rows - wh)/s) + 1 (likewise for columns).
+bool on_lattice(const Handle *h, const WinDesc &d, WinDesc *out)
+{
+    const int64_t st = h->lat_s;
+    if (!st || d.sy != st || d.sx != st || d.wh % st || d.ww % st || d.row0 != 0) return false;
+    WinDesc x = d;
+    x.wh = d.wh / st;
+    x.ww = d.ww / st;
+    x.sy = 1;
+    x.sx = 1;
+    x.area = (uint64_t)(d.wh * d.ww);
+    if (h->lat_rows - x.wh + 1 != d.R || h->lat_cols - x.ww + 1 != d.C) return false;
+    *out = x;
+    return true;
+}
+
+// The lattice flag for a set of queries: SWA_LATTICE(s) for the stride s
+// (8..255) at which the most queries have strides (s, s) and sides that are
+// multiples of s, or 0 if none has.
+uint32_t lattice_for(const swa_window *w, int n)
+{
+    int64_t best = 0;
+    int best_n = 0;
+    for (int k = 0; k < n; ++k) {
+        const int64_t st = w[k].sy;
+        if (st < 8 || st > 255 || w[k].sx != st || w[k].wh % st || w[k].ww % st) continue;
+        int c = 0;
+        for (int q = 0; q < n; ++q)
+            c += w[q].sy == st && w[q].sx == st && w[q].wh % st == 0 && w[q].ww % st == 0;
+        if (c > best_n) { best_n = c; best = st; }
+    }
+    return best ? SWA_LATTICE(best) : 0u;
 }
 
 // Order `s` after the build, run the windows, then join `s` back into the
@@ -114,7 +155,15 @@ swa_status run_windows(const Handle *h, const WinDesc *d, int n, cudaStream_t s)
             (e = cudaStreamWaitEvent(s, hm->use_event, 0)) != cudaSuccess)
             return cuda_fail(e, "ordering after the build");
     }
-    swa_status st = launch_windows(h->S, h->Q, h->ld, d, n, s);
+    // Queries the corner lattice serves go in a launch of their own on it.
+    WinDesc lat[SWA_MAX_WINDOWS], rest[SWA_MAX_WINDOWS];
+    int nl = 0, nr = 0;
+    for (int k = 0; k < n; ++k)
+        if (!on_lattice(h, d[k], &lat[nl])) rest[nr++] = d[k];
+        else ++nl;
+    swa_status st = SWA_OK;
+    if (nl) st = launch_windows(h->LS, h->LQ, h->lat_ld, lat, nl, s);
+    if (st == SWA_OK && nr) st = launch_windows(h->S, h->Q, h->ld, rest, nr, s);
     if (st != SWA_OK) return st;
     if (s != h->stream) {
         if ((e = cudaEventRecord(hm->use_event, s)) != cudaSuccess ||
@@ -327,10 +376,12 @@ swa_status swa_window_shape(int64_t rows, int64_t cols, int64_t wh, int64_t ww, 
 swa_status swa_sat_bytes(int64_t rows, int64_t cols, swa_dtype dtype, uint32_t flags,
                          int64_t *table_bytes, int64_t *scratch_bytes)
 {
-    if (rows <= 0 || cols <= 0 || (dtype != SWA_U8 && dtype != SWA_U16) || (flags & ~3u))
+    if (rows <= 0 || cols <= 0 || (dtype != SWA_U8 && dtype != SWA_U16) ||
+        (flags & ~(3u | SWA_LATTICE_MASK)))
         return SWA_EINVAL;
     BuildPlan p = make_plan(rows, cols, cols * pixel_bytes(dtype), dtype, flags, nullptr);
-    if (table_bytes) *table_bytes = p.ld * rows * 8 * (p.with_q ? 2 : 1);
+    if (table_bytes)
+        *table_bytes = p.ld * rows * 8 * (p.with_q ? 2 : 1) + 2 * p.lat_rows * p.lat_ld * 8;
     if (scratch_bytes) *scratch_bytes = p.scratch_bytes;
     return SWA_OK;
 }
@@ -373,9 +424,16 @@ swa_status build_handle(const void *d_image, int64_t rows, int64_t cols, int64_t
 {
     if (out) *out = nullptr;
     if (!d_image || !out || rows <= 0 || cols <= 0 || (dtype != SWA_U8 && dtype != SWA_U16) ||
-        (flags & ~3u) || pitch_bytes < cols * pixel_bytes(dtype)) {
+        (flags & ~(3u | SWA_LATTICE_MASK)) || pitch_bytes < cols * pixel_bytes(dtype)) {
         set_error("bad build arguments");
         return SWA_EINVAL;
+    }
+    if (const uint32_t ls = (flags & SWA_LATTICE_MASK) >> SWA_LATTICE_SHIFT) {
+        if (ls < 8 || !(flags & SWA_WITH_SQ) || (flags & SWA_TWOPASS) || count) {
+            set_error("a corner lattice needs a stride of 8 to 255, SWA_WITH_SQ and the "
+                      "single-pass build");
+            return SWA_EINVAL;
+        }
     }
     if (dtype == SWA_U16 && ((uintptr_t)d_image % 2 || pitch_bytes % 2)) {
         set_error("uint16 images need a 2-byte aligned base and an even pitch");
@@ -391,10 +449,11 @@ swa_status build_handle(const void *d_image, int64_t rows, int64_t cols, int64_t
     BuildPlan p = make_plan(rows, cols, pitch_bytes, dtype, count ? kCountPlan : flags, d_image);
     p.thr = thr;
     const int64_t tbytes = p.ld * rows * 8;
+    const int64_t lbytes = p.lat_rows * p.lat_ld * 8;     // one lattice array
     const int64_t lim = g_limit.load();
-    if (lim == 0 || (lim > 0 && tbytes * (wq ? 2 : 1) + p.scratch_bytes > lim)) {
+    if (lim == 0 || (lim > 0 && tbytes * (wq ? 2 : 1) + 2 * lbytes + p.scratch_bytes > lim)) {
         set_error("memory limit %lld bytes < %lld needed", (long long)lim,
-                  (long long)(tbytes * (wq ? 2 : 1) + p.scratch_bytes));
+                  (long long)(tbytes * (wq ? 2 : 1) + 2 * lbytes + p.scratch_bytes));
         return SWA_ENOMEM;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -407,7 +466,7 @@ swa_status build_handle(const void *d_image, int64_t rows, int64_t cols, int64_t
     h->dtype = dtype;
     h->flags = count ? (SWA_WITH_SQ | SWA_COUNT) : flags;
     h->stream = s;
-    h->table_bytes = tbytes * (wq ? 2 : 1);
+    h->table_bytes = tbytes * (wq ? 2 : 1) + 2 * lbytes;
     cudaError_t e = cudaGetDevice(&h->device);
     swa_status st = SWA_OK;
     void *mem = nullptr;
@@ -424,6 +483,18 @@ swa_status build_handle(const void *d_image, int64_t rows, int64_t cols, int64_t
         h->Q = static_cast<uint64_t *>(mem);
     }
     if (count) h->Q = h->S;
+    if (lbytes) {
+        if (dev_alloc(&mem, lbytes, s, &st) != cudaSuccess) goto fail;
+        h->LS = static_cast<uint64_t *>(mem);
+        if (dev_alloc(&mem, lbytes, s, &st) != cudaSuccess) goto fail;
+        h->LQ = static_cast<uint64_t *>(mem);
+        h->lat_s = p.lat_s;
+        h->lat_rows = p.lat_rows;
+        h->lat_cols = p.lat_cols;
+        h->lat_ld = p.lat_ld;
+        p.lat_S = h->LS;
+        p.lat_Q = h->LQ;
+    }
     if (dev_alloc(&mem, 256, s, &st) != cudaSuccess) goto fail;
     h->d_err = static_cast<uint32_t *>(mem);
     if ((e = cudaMemsetAsync(h->d_err, 0, 256, s)) != cudaSuccess) {
@@ -446,6 +517,8 @@ fail:
     if (scratch) dev_free(scratch, p.scratch_bytes, s);
     if (h->S) dev_free(h->S, tbytes, s);
     if (h->Q && h->Q != h->S) dev_free(h->Q, tbytes, s);
+    if (h->LS) dev_free(h->LS, lbytes, s);
+    if (h->LQ) dev_free(h->LQ, lbytes, s);
     if (h->d_err) dev_free(h->d_err, 256, s);
     if (h->use_event) cudaEventDestroy(h->use_event);
     h->tag = kFreedTag;
@@ -511,6 +584,20 @@ swa_status swa_sat_data(const swa_sat *sat, const uint64_t **d_S, const uint64_t
     if (d_S) *d_S = h->S;
     if (d_Q) *d_Q = h->Q;
     if (ld) *ld = h->ld;
+    return SWA_OK;
+}
+
+swa_status swa_sat_lattice(const swa_sat *sat, const uint64_t **d_LS, const uint64_t **d_LQ,
+                           int64_t *rows, int64_t *cols, int64_t *ld, int32_t *stride)
+{
+    if (!live(sat)) return SWA_EINVAL;
+    const Handle *h = reinterpret_cast<const Handle *>(sat);
+    if (d_LS) *d_LS = h->LS;
+    if (d_LQ) *d_LQ = h->LQ;
+    if (rows) *rows = h->lat_rows;
+    if (cols) *cols = h->lat_cols;
+    if (ld) *ld = h->lat_ld;
+    if (stride) *stride = h->lat_s;
     return SWA_OK;
 }
 
@@ -584,6 +671,8 @@ void swa_free(swa_sat *sat)
     const int64_t tb = h->ld * h->rows * 8;
     dev_free(h->S, tb, h->stream);
     if (h->Q && h->Q != h->S) dev_free(h->Q, tb, h->stream);
+    if (h->LS) dev_free(h->LS, h->lat_rows * h->lat_ld * 8, h->stream);
+    if (h->LQ) dev_free(h->LQ, h->lat_rows * h->lat_ld * 8, h->stream);
     dev_free(h->d_err, 256, h->stream);
     cudaEventDestroy(h->use_event);
     h->tag = kFreedTag;
@@ -666,6 +755,9 @@ swa_status swa_analyze(const void *image, int64_t rows, int64_t cols, int64_t pi
         }
         dw[k].out_ld = C;
     }
+    // Queries that all their corners' lattice serves read it instead of the
+    // tables (the lattice needs Q, which std already asks for).
+    if (flags & SWA_WITH_SQ) flags |= lattice_for(windows, n);
     if ((st = swa_build_sat(d_img, rows, cols, dpitch, dtype, flags, stream, &sat)) != SWA_OK)
         goto done;
     if ((st = swa_window_stats_multi(sat, dw.data(), n, stream)) != SWA_OK) goto done;

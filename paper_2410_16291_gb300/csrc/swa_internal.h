@@ -35,6 +35,12 @@ struct BuildPlan {
     bool count;           // table of the indicator "pixel > thr" (S only)
     uint32_t thr;
     bool corner;          // single pass: corner term from corner records (wide images)
+    // Corner lattice (single pass with Q): stride (0: none), its size and the
+    // caller's arrays for it (S and Q entries at rows and columns one below a
+    // multiple of the stride).
+    int lat_s;
+    int64_t lat_rows, lat_cols, lat_ld;
+    uint64_t *lat_S, *lat_Q;
 };
 
 struct Handle {
@@ -44,6 +50,9 @@ struct Handle {
     int dtype;
     uint32_t flags;
     uint64_t *S, *Q;          // device tables (Q may be null)
+    uint64_t *LS, *LQ;        // corner lattice of S and Q (null without one)
+    int64_t lat_rows, lat_cols, lat_ld;
+    int32_t lat_s;            // lattice stride (0: none)
     char *scratch;            // carries, tile status, error word
     int64_t scratch_bytes, table_bytes;
     uint32_t *d_err;          // device error word (inside scratch)
@@ -102,6 +111,8 @@ swa_status launch_build(const BuildPlan &p, const void *image, uint64_t *S,
 struct WinDesc {
     int64_t wh, ww, sy, sx, R, C, out_ld;
     int64_t row0;
+    uint64_t area;        // window area for the moments (0: wh * ww); a query on a
+                          // corner lattice has the lattice's window sides
     uint32_t outputs;
     uint32_t vmax;        // largest pixel value of the table's image (255,
                           // 65535, 1 for a count table; 0: unknown)

@@ -419,8 +419,11 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
     // Rounding path of query k: the integer one for areas below 2^32, with
     // D in 64 bits when n times the largest pixel value stays below 2^32
     // (and std is asked for); FP64 for larger areas.
+    auto area_of = [&](int k) {
+        return w[k].area ? w[k].area : (uint64_t)(w[k].wh * w[k].ww);
+    };
     auto mode_of = [&](int k) {
-        const uint64_t area = (uint64_t)(w[k].wh * w[k].ww);
+        const uint64_t area = area_of(k);
         if (area >= (1ull << 32)) return kRnFp64;
         const bool d64 = (w[k].outputs & SWA_OUT_STD) && w[k].vmax &&
                          area * (uint64_t)w[k].vmax < (1ull << 32);
@@ -480,7 +483,7 @@ swa_status launch_windows(const uint64_t *S, const uint64_t *Q, int64_t ld, cons
             blocks += R * g.nbx;
             for (int t = 0; t < m; ++t) {
                 const int k = members[t];
-                const uint64_t area = (uint64_t)(w[k].wh * w[k].ww);
+                const uint64_t area = area_of(k);
                 WinQ &q = a.q[a.nq++];
                 q.w = w[k];
                 q.n = area;

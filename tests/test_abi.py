@@ -127,3 +127,23 @@ def test_batch_config_checked_on_the_host(L):
         assert L.swa_batch_create(items, 1, ctypes.byref(cfg), None, ctypes.byref(h)) == \
             swa.SWA_EINVAL, bad
         assert h.value is None
+
+
+def test_lattice_flag_checks_on_the_host(L):
+    """The corner-lattice build flag is refused without Q, with the two-pass
+    build or with a stride outside 8..255, before any device work; the table
+    byte count includes the two lattice arrays."""
+    h = ctypes.c_void_p()
+    img = ctypes.c_void_p(0x1000)
+    for flags in [8 << 8, swa.SWA_WITH_SQ | (7 << 8), swa.SWA_WITH_SQ | swa.SWA_TWOPASS | (16 << 8),
+                  swa.SWA_WITH_SQ | (1 << 16)]:
+        assert L.swa_build_sat(img, 100, 100, 100, swa.SWA_U8, flags, None,
+                               ctypes.byref(h)) == swa.SWA_EINVAL, hex(flags)
+        assert h.value is None
+    t0, t1, sc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    assert L.swa_sat_bytes(70000, 85000, swa.SWA_U8, swa.SWA_WITH_SQ, ctypes.byref(t0),
+                           ctypes.byref(sc)) == swa.SWA_OK
+    assert L.swa_sat_bytes(70000, 85000, swa.SWA_U8, swa.SWA_WITH_SQ | (16 << 8), ctypes.byref(t1),
+                           ctypes.byref(sc)) == swa.SWA_OK
+    ld = (85000 // 16 + 31) // 32 * 32
+    assert t1.value - t0.value == 2 * (70000 // 16) * ld * 8
