@@ -81,8 +81,10 @@ enum {
  * lies on that lattice (top-left pixel (s*i, s*j): corner rows s*i - 1 and
  * s*i + wh - 1), so swa_window_stats* evaluates such queries from the
  * lattice, reading dense rows instead of one scattered entry per 64-byte
- * line; results are the same.  Needs SWA_WITH_SQ, not SWA_TWOPASS.  The
- * paper's corner lookup (Section II-B) on a subsampled table. */
+ * line; results are the same.  Needs SWA_WITH_SQ, not SWA_TWOPASS.  Images
+ * of 2^31 rows or columns or more, or smaller than s in either direction,
+ * get no lattice (swa_sat_lattice reports stride 0).  The paper's corner
+ * lookup (Section II-B) on a subsampled table. */
 #define SWA_LATTICE(s) ((uint32_t)(s) << SWA_LATTICE_SHIFT)
 
 /* Window output selection. */

@@ -528,6 +528,7 @@ BuildPlan make_plan(int64_t rows, int64_t cols, int64_t pitch, int dtype, uint32
     // caller supplies the lattice arrays (lat_S, lat_Q, lat_ld).
     p.lat_s = (!p.twopass && !p.count && p.with_q) ? (int)((flags >> SWA_LATTICE_SHIFT) & 0xffu)
                                                    : 0;
+    if (rows >= (1ll << 31) || cols >= (1ll << 31)) p.lat_s = 0;   // 32-bit lattice indices
     p.lat_rows = p.lat_s ? rows / p.lat_s : 0;
     p.lat_cols = p.lat_s ? cols / p.lat_s : 0;
     if (!p.lat_rows || !p.lat_cols) p.lat_s = 0;

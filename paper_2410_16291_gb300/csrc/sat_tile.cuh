@@ -806,25 +806,26 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     if (!lookback_tile<WQ, TH>(a, t, b, s, cs, cq, rs_s, rs_q, err, vs, vq, lr_s, lr_q))
         return false;
 
-    // Corner lattice: the tile's first lattice row and lattice row index, the
-    // lane's lattice column (lat_k: its position among the lane's 8 columns,
-    // -1 if none) and lattice column index.
-    int64_t lat_y = 0, lat_i = 0, lat_j = 0;
+    // Corner lattice: the tile's first lattice row lat_y, the offset of the
+    // lane's entry in that lattice row, and lat_k, the lane's lattice column
+    // among its 8 columns (-1 if none).  Row and column indices are below
+    // 2^31 for lattice builds, so 32-bit divisions find them (two per tile).
+    uint32_t lat_y = 0;
+    int64_t lat_off = 0;
     int lat_k = -1;
     if (LAT) {
-        const int64_t st = a.lat_stride;
-        lat_y = (y0 + st) / st * st - 1;              // first y >= y0 with st | y + 1
-        lat_i = (lat_y + 1) / st - 1;
-        const int64_t xn = (x + st) / st * st - 1;    // first column >= x likewise
-        if (xn < x + kPxPerLane && xn < a.cols) {
-            lat_k = (int)(xn - x);
-            lat_j = (xn + 1) / st - 1;
-        }
+        const uint32_t st = (uint32_t)a.lat_stride;
+        const uint32_t qy = ((uint32_t)y0 + st) / st;         // first y >= y0 with st | y + 1
+        lat_y = qy * st - 1;
+        const uint32_t qx = ((uint32_t)x + st) / st;          // first column >= x likewise
+        const int64_t xn = (int64_t)qx * st - 1;
+        if (xn < x + kPxPerLane && xn < a.cols) lat_k = (int)(xn - x);
+        lat_off = (int64_t)(qy - 1) * a.lat_ld + (qx - 1);
     }
     // Writes the lane's lattice entry of row y (values as emit_row forms them).
     auto lat_row = [&](int64_t y, uint64_t base_s, const uint32_t *lp, uint64_t base_q,
                        const QA *lq) {
-        if (!LAT || y != lat_y) return;
+        if (!LAT || (uint32_t)y != lat_y) return;
         if (lat_k >= 0) {
             uint64_t vS = 0, vQ = 0;
 #pragma unroll
@@ -833,12 +834,11 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
                     vS = base_s + vs[k] + lp[k];
                     if (WQ) vQ = base_q + vq[k] + (uint64_t)lq[k];
                 }
-            const int64_t off = lat_i * a.lat_ld + lat_j;
-            a.lat_s[off] = vS;
-            if (WQ) a.lat_q[off] = vQ;
+            a.lat_s[lat_off] = vS;
+            if (WQ) a.lat_q[lat_off] = vQ;
         }
-        lat_y += a.lat_stride;
-        ++lat_i;
+        lat_y += (uint32_t)a.lat_stride;
+        lat_off += a.lat_ld;
     };
 
     // Rows go in pairs: the two rows' prefix and warp-scan chains are
