@@ -208,6 +208,30 @@ swa_status swa_window_stats_multi(const swa_sat *sat, const swa_window *windows,
 swa_status swa_sat_data(const swa_sat *sat, const uint64_t **d_S,
                         const uint64_t **d_Q, int64_t *ld);
 
+/*
+ * Check tables against their image on the device, by the recurrence that
+ * defines the summed-area table (Section II-B):
+ *   S[y][x] - S[y][x-1] - S[y-1][x] + S[y-1][x-1] == I[y][x]  (mod 2^64),
+ * index -1 reading as 0, and Q likewise with I[y][x]^2.  Tables that pass
+ * everywhere are exactly the image's tables (induction over rows, then
+ * columns; no entry reaches 2^64 under the overflow bound), so this checks
+ * a whole build in place, without copying tables to the host.
+ *   d_image, rows, cols, pitch_bytes, dtype: the image, as for swa_build_sat.
+ *   d_S, d_Q     the tables (device, leading dimension ld >= cols); d_Q may
+ *                be NULL (S only).  Any table will do: a handle's
+ *                (swa_sat_data), a batch's (swa_batch_tables), a caller's.
+ *   d_counts     caller device array of 3 uint64, written on `stream`: [0]
+ *                S entries failing, [1] Q entries failing, [2] the smallest
+ *                y * cols + x of a failing entry (UINT64_MAX if none).
+ * Enqueues one kernel on `stream` (after two memsets) and returns; SWA_EINVAL
+ * for bad arguments.  No paper counterpart beyond the definition: a
+ * self-check for tests and for users who want to validate a build.
+ */
+swa_status swa_verify_tables(const void *d_image, int64_t rows, int64_t cols,
+                             int64_t pitch_bytes, swa_dtype dtype, const uint64_t *d_S,
+                             const uint64_t *d_Q, int64_t ld, uint64_t *d_counts,
+                             swa_stream stream);
+
 /* Borrowed device views of the corner lattice (see SWA_LATTICE): lattice
  * entry (a, b) of S is S[s*(a+1) - 1][s*(b+1) - 1], for a < rows / s and
  * b < cols / s, at d_LS[a * ld + b] (d_LQ likewise for Q).  A handle built

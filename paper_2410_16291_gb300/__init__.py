@@ -95,6 +95,8 @@ SIGNATURES = {
     "swa_build_sat_noalloc": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _U32, _VP, _VP,
                                              _I64, _VP, _VP]),
     "swa_profile_end": (_I32, [_P(swa_kernel_time), _I32]),
+    "swa_verify_tables": (ctypes.c_int, [_VP, _I64, _I64, _I64, ctypes.c_int, _VP, _VP, _I64,
+                                         _VP, _VP]),
 }
 
 _lib = None
@@ -270,6 +272,27 @@ class SAT:
             self.free()
         except Exception:
             pass
+
+
+def verify_tables(image, S, Q=None, stream=None):
+    """Check tables against a 2-D uint8/uint16 CUDA image on the device by
+    the summed-area recurrence (see swa_verify_tables): returns (S entries
+    failing, Q entries failing, smallest failing flat index or None).  S and
+    Q are int64 views (uint64 bit patterns) with unit column stride, e.g.
+    from SAT.tables() or Batch.tables()."""
+    import torch
+    assert image.is_cuda and image.dim() == 2 and image.stride(1) == 1
+    rows, cols = image.shape
+    assert S.shape == (rows, cols) and S.stride(1) == 1
+    if Q is not None:
+        assert Q.shape == (rows, cols) and Q.stride(1) == 1 and Q.stride(0) == S.stride(0)
+    counts = torch.empty(3, dtype=torch.int64, device=image.device)
+    check(lib().swa_verify_tables(image.data_ptr(), rows, cols,
+                                  image.stride(0) * image.element_size(), _dtype_code(image),
+                                  S.data_ptr(), None if Q is None else Q.data_ptr(), S.stride(0),
+                                  counts.data_ptr(), _stream_ptr(stream)), "swa_verify_tables")
+    c = counts.cpu().tolist()
+    return c[0], c[1], (None if c[2] == -1 else c[2])
 
 
 def _view_u64(ptr, rows, cols, ld):

@@ -147,3 +147,15 @@ def test_lattice_flag_checks_on_the_host(L):
                            ctypes.byref(sc)) == swa.SWA_OK
     ld = (85000 // 16 + 31) // 32 * 32
     assert t1.value - t0.value == 2 * (70000 // 16) * ld * 8
+
+
+def test_verify_tables_argument_checks(L):
+    """Bad arguments are refused before any device work."""
+    img, S = ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000)
+    cnt = ctypes.c_void_p(0x3000)
+    assert L.swa_verify_tables(None, 4, 4, 4, swa.SWA_U8, S, None, 4, cnt, None) == swa.SWA_EINVAL
+    assert L.swa_verify_tables(img, 4, 4, 4, swa.SWA_U8, S, None, 3, cnt, None) == swa.SWA_EINVAL
+    assert L.swa_verify_tables(img, 4, 4, 3, swa.SWA_U8, S, None, 4, cnt, None) == swa.SWA_EINVAL
+    assert L.swa_verify_tables(img, 4, 4, 8, swa.SWA_U8, S, None, 4, None, None) == swa.SWA_EINVAL
+    assert L.swa_verify_tables(ctypes.c_void_p(0x1001), 4, 4, 8, swa.SWA_U16, S, None, 4, cnt,
+                               None) == swa.SWA_EINVAL

@@ -45,13 +45,15 @@ def test_workload1_20k():
     for bit against the oracle; random windows also by the definition."""
     (im,) = synth.workload(1)
     img = im.generate()
-    sat = swa.build_sat(to_device(img))
+    dev = to_device(img)
+    sat = swa.build_sat(dev)
     wins = [(w.wh, w.ww, w.sy, w.sx) for w in im.windows]
     res = sat.window_stats(wins)
     S_ref, Q_ref = oracle.sat(img)
     S, Q = sat.tables()
     np.testing.assert_array_equal(u64(S), S_ref)
     np.testing.assert_array_equal(u64(Q), Q_ref)
+    assert swa.verify_tables(dev, S, Q) == (0, 0, None)
     del S_ref, Q_ref, S, Q
     assert full_parity.check_all_windows(img, wins, res) == 1186171803
     sampled_windows(img, res, wins, 200)
@@ -60,7 +62,8 @@ def test_workload1_20k():
 
 def test_workload2_70k_by_85k():
     """70,000 x 85,000 u8 (5.95e9 px, 95 GB of tables), built with the corner
-    lattice of stride 16 as the benchmark does: sampled table rows streamed by
+    lattice of stride 16 as the benchmark does: every table entry checked on
+    the device by the summed-area recurrence, sampled table rows streamed by
     the oracle, last entries equal the totals, the lattice equal to the
     sampled rows at its columns, every one of the 45,728,608 windows (256 and
     1024 at stride 16, served from the lattice) against the oracle's
@@ -74,6 +77,8 @@ def test_workload2_70k_by_85k():
     res = sat.window_stats(wins)
     sat.sync()
     S, Q = sat.tables()
+    # every entry of both 47.6 GB tables, on the device, by the recurrence
+    assert swa.verify_tables(dev, S, Q) == (0, 0, None)
     rows = [0, 1, 127, 128, 4095, 35001, 35007, 69998, 69999]
     S_ref, Q_ref = oracle.sat_rows(img, rows)
     np.testing.assert_array_equal(u64(S[rows]), S_ref)
@@ -109,6 +114,7 @@ def test_u16_all_max_at_the_overflow_edge():
     dev = torch.full((r, c), -1, dtype=torch.int16, device="cuda")   # 0xFFFF
     sat = swa.build_sat(dev)
     S, Q = sat.tables()
+    assert swa.verify_tables(dev, S, Q) == (0, 0, None)          # every entry
     v = 65535
     assert int(u64(S[-1:, -1:])[0, 0]) == r * c * v
     assert int(u64(Q[-1:, -1:])[0, 0]) == r * c * v * v

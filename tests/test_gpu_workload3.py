@@ -4,7 +4,9 @@
 autotuned configuration, replayed from a captured CUDA graph.
 
 - On the device, every table entry and every output equals a per-image
-  ``swa_build_sat`` + ``swa_window_stats`` run, bit for bit.
+  ``swa_build_sat`` + ``swa_window_stats`` run, bit for bit, and every
+  table entry satisfies the summed-area recurrence with the image
+  (``swa_verify_tables``).
 - Against the oracle: each image's last table entries equal its totals,
   four table rows per image equal the oracle's streamed rows, and every one
   of the 2.29e9 window outputs (sum, mean, std) equals the oracle's
@@ -72,6 +74,7 @@ def test_workload3_batch_every_table_and_window():
         S, Q = sat.tables()
         bS, bQ = b.tables(k)
         assert torch.equal(S, bS) and torch.equal(Q, bQ), k
+        assert swa.verify_tables(dev, bS, bQ) == (0, 0, None), k
         for q, (got, ref) in enumerate(zip(b.outputs[k], sat.window_stats(wins[k]))):
             for key in ("sum", "mean", "std"):
                 assert torch.equal(got[key], ref[key]), (k, q, key)
