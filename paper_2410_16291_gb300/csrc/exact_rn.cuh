@@ -377,10 +377,12 @@ SWA_HD double std_rn(uint64_t n, uint64_t sw, uint64_t qw, const Divisor &D)
 
 // std_rn for windows whose products n*qw and sw*sw both stay below 2^64
 // (n times the largest pixel value below 2^32): D is formed in 64 bits, the
-// roundings are std_rn's.
+// roundings are std_rn's.  n and sw are then below 2^32, so each product
+// takes one 32 x 64 (n * qw) or 32 x 32 (sw * sw) multiplication.
 SWA_HD double std_rn64(uint64_t n, uint64_t sw, uint64_t qw, const Divisor &D)
 {
-    const uint64_t d = n * qw - sw * sw;
+    const uint32_t n32 = (uint32_t)n, s32 = (uint32_t)sw;
+    const uint64_t d = (uint64_t)n32 * qw - (uint64_t)s32 * s32;
     if (d == 0) return 0.0;
     const Fp r = round_u64(d);
     const Fp s = sqrt_rn(r.sig, r.exp);
