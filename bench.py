@@ -37,6 +37,11 @@ METRIC = "SAT build Gpx/s + window outputs/s, % HBM peak; served p50/p99 vs plai
 # the window kernel, from ncu on the 12,288^2 stride-1 case
 # (profiles/window_stats_dense_12288x12288.md).
 INSTR_PER_WINDOW = 400.6
+# The same for windows served from the corner lattice of the default
+# workload (window areas 256^2 and 1024^2, powers of two: the divisions are
+# exact shifts), from ncu on the 8,192 x 16,384 case with windows 256/1024 at
+# stride 16 (profiles/window_stats_lattice_8192x16384.md).
+INSTR_PER_WINDOW_LATTICE_POW2 = 296.0
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e datasheet bandwidth, for context beside the measured peak
 
@@ -183,6 +188,30 @@ def distinct_corner_bytes(rows, cols, wh, ww, sy, sx, tables):
     ry = np.unique(np.concatenate([i * sy - 1, i * sy + wh - 1]))
     cx = np.unique(np.concatenate([j * sx - 1, j * sx + ww - 1]))
     return int((ry >= 0).sum()) * int((cx >= 0).sum()) * 8 * tables
+
+
+def distinct_corner_bytes_all(rows, cols, windows, tables):
+    """Bytes of the distinct table entries a set of window queries reads
+    together: each query's corners are the product of its corner rows and
+    corner columns, and the union of the products is counted by
+    inclusion-exclusion over subsets of the queries."""
+    import itertools
+    sets = []
+    for wh, ww, sy, sx in windows:
+        i = np.arange((rows - wh) // sy + 1, dtype=np.int64)
+        j = np.arange((cols - ww) // sx + 1, dtype=np.int64)
+        ry = np.unique(np.concatenate([i * sy - 1, i * sy + wh - 1]))
+        cx = np.unique(np.concatenate([j * sx - 1, j * sx + ww - 1]))
+        sets.append((ry[ry >= 0], cx[cx >= 0]))
+    total = 0
+    for k in range(1, len(sets) + 1):
+        for sub in itertools.combinations(sets, k):
+            ry, cx = sub[0]
+            for r2, c2 in sub[1:]:
+                ry = np.intersect1d(ry, r2, assume_unique=True)
+                cx = np.intersect1d(cx, c2, assume_unique=True)
+            total += (-1) ** (k + 1) * len(ry) * len(cx)
+    return total * 8 * tables
 
 
 def traffic_record(kernel, case=None):
@@ -437,8 +466,8 @@ def run_ours(args, rank, world, local_rank):
     dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
     bytes_per_launch = {"sat_build": build_bytes, "sat_scan": build_bytes,
                         "sat_reduce": px * 1}
-    win_bytes = sum(distinct_corner_bytes(im.rows, im.cols, *w, tables) + 24 * R * C
-                    for w, (R, C) in zip(windows, shapes))
+    win_bytes = (distinct_corner_bytes_all(im.rows, im.cols, windows, tables) +
+                 sum(24 * R * C for R, C in shapes))
     win_launches = kernels.get("window_stats", {}).get("launches", 0)
     bytes_per_launch["window_stats"] = win_bytes * args.steps / max(1, win_launches)
     roof = None
@@ -470,6 +499,24 @@ def run_ours(args, rank, world, local_rank):
                     "count" if args.threshold is not None else
                     ("two-pass S+Q" if args.twopass else
                      "S+Q" + (" lattice %d" % lat if lat else "")))), "avg_ms": avg}
+    # The window step beside the build: algorithmic bytes (outputs and the
+    # distinct table entries the corners read, once) against HBM, and the
+    # issue rate its exact arithmetic needs.
+    win_roof = None
+    if "window_stats" in kernels and kernels.get("window_stats", {}).get("launches"):
+        w_ms = kernels["window_stats"]["avg_ms"] * win_launches / args.steps
+        n_win = sum(R * C for R, C in shapes)
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        pow2 = all((w[0] * w[1]) & (w[0] * w[1] - 1) == 0 for w in windows)
+        ipw = INSTR_PER_WINDOW_LATTICE_POW2 if (lat and pow2) else INSTR_PER_WINDOW
+        win_roof = {"ms_per_step": w_ms, "windows": n_win,
+                    "algorithmic_bytes": win_bytes, "bytes_per_window": win_bytes / n_win,
+                    "hbm_achieved_gbs": win_bytes / (w_ms / 1e3) / 1e9,
+                    "hbm_frac": win_bytes / (w_ms / 1e3) / 1e9 / hbm,
+                    "instructions_per_window": ipw,
+                    "issue_frac": n_win * ipw / (w_ms / 1e3) / (sms * 4 * 32 * mhz * 1e6),
+                    "source": "corner lattice" if lat else "tables"}
     build_ms = sum(kernels[k]["avg_ms"] * kernels[k]["launches"] for k in kernels
                    if k.startswith("sat_")) / args.steps
     win_ms = sum(kernels[k]["avg_ms"] * kernels[k]["launches"] for k in kernels
@@ -536,7 +583,8 @@ def run_ours(args, rank, world, local_rank):
             "sat_build_ms": build_ms, "window_ms": win_ms,
             "window_outputs_per_s": world * n_out / (ms / 1e3),
             "window_outputs_per_step": n_out,
-            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "window_roofline": win_roof, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": launches, **sub,
             "build_path": "twopass" if args.twopass else "default",
             "lattice_stride": lat}
