@@ -410,7 +410,7 @@ def run_ours(args, rank, world, local_rank):
     # can use it (strides (s, s), sides multiples of s, 8 <= s <= 255).
     lat = 0
     strides = {(w[2], w[3]) for w in windows}
-    if len(strides) == 1 and not args.twopass and not args.no_lattice:
+    if len(strides) == 1 and not args.twopass and not args.no_lattice and args.threshold is None:
         sy, sx = strides.pop()
         if sy == sx and 8 <= sy <= 255 and all(w[0] % sy == 0 and w[1] % sy == 0
                                                for w in windows):
