@@ -161,8 +161,7 @@ swa_status swa_build_count_sat(const void *d_image, int64_t rows, int64_t cols,
  *                the fixed scratch array, which the next call clears.
  * Scratch lives in one fixed 64 MiB device array inside the library, which
  * every device that loads the library holds until the process exits.  An
- * image needing more (about 100 million uint8 or 58 million uint16
- * pixels) is rejected with SWA_EINVAL and a message; use swa_build_sat.  All
+ * image needing more (about 100 million pixels of either type) is rejected with SWA_EINVAL and a message; use swa_build_sat.  All
  * calls share the array: calls whose builds overlap on the GPU (concurrent
  * streams, or several host threads) race and must be serialized by the
  * caller.  The first call on each device looks up the array's address

@@ -408,7 +408,9 @@ swa_status dispatch_twopass(const BuildPlan &p, const char *img, uint64_t *S, ui
                  : launch_twopass<T, false, false>(p, img, S, Q, scratch, st);
 }
 
-template <typename T> constexpr int onepass_rows() { return sizeof(T) == 1 ? 64 : 32; }
+// Rows per single-pass tile: 64 for both pixel types (uint16 tiles are staged
+// in two 32-row parts, see onepass_tile).
+template <typename T> constexpr int onepass_rows() { return 64; }
 
 // Warps per block of the single-pass build: as many independent warps as
 // the shared memory of one SM holds (227 KB per block, 1 KB for alignment),

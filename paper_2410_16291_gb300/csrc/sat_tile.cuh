@@ -135,6 +135,11 @@ __device__ __forceinline__ void smem8(const T *row, int lane, uint32_t px[8])
 template <typename T>
 constexpr int tile_row_bytes() { return kSliceCols * (int)sizeof(T) + 16; }
 
+// Rows of a TH-row tile staged at a time: all of them while they hold at most
+// 16 KB of pixels (256 columns of uint8 up to 64 rows), else 32-row parts.
+template <typename T, int TH>
+constexpr int staged_rows() { return TH * (int)sizeof(T) <= 64 ? TH : 32; }
+
 // The lane's 8 pixels of one staged row.  VEC rows hold the slice's pixels
 // from byte 0; other rows hold the 16-byte-aligned chunks covering the
 // slice, whose pixels start m bytes in (m = the row's misalignment, 0..15).
@@ -668,6 +673,15 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     constexpr int RPL = TH / 32;                       // rows each lane keeps
     const int lane = threadIdx.x & 31;
     constexpr int RB = tile_row_bytes<T>();
+    // Rows staged at a time: the whole tile, or 32-row parts of it when its
+    // pixels exceed 16 KB (uint16 64-row tiles), so the staging buffer and
+    // the warps per SM stay those of the uint8 tile.  Parts are staged and
+    // reduced bottom part first, so the top part is still staged when the
+    // scan begins; the other parts are staged again for their scan (from L2,
+    // which has just read them).
+    constexpr int SR = staged_rows<T, TH>();
+    constexpr int GPP = SR / 32;                       // 32-row groups per staged part
+    static_assert(SR % 32 == 0 && TH % SR == 0, "staged parts are whole 32-row groups");
     unsigned char *tile = w.tile;
     const int64_t b = t / a.nsx, s = t % a.nsx;
     const int64_t y0 = b * TH;
@@ -689,7 +703,8 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
         }
     };
 
-    // Stage the tile (rows 0..nr-1; columns past the image read as 0).  With
+    // Stage rows r0 .. min(nr, r0 + SR) - 1 of the tile into buffer rows 0, 1,
+    // ... (columns past the image read as 0).  With
     // VEC every lane copies its 8 pixels with one cp.async.  Otherwise a row
     // may start at any (even, for uint16) byte address: the warp copies the
     // 16-byte-aligned chunks covering the slice (uint8: 17 chunks, lanes
@@ -698,8 +713,10 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     // the row are zero-filled here; pieces that straddle an end of the row
     // are left for the pass below, which loads their bytes one row per lane.
     constexpr int NCH = kSliceCols * (int)sizeof(T) / 16 + 1;
-    for (int r = 0; r < nr; ++r) {
-        unsigned char *drow = tile + r * RB;
+    auto stage = [&](int r0) {
+    const int r1 = min(nr, r0 + SR);
+    for (int r = r0; r < r1; ++r) {
+        unsigned char *drow = tile + (r - r0) * RB;
         const char *row = a.img + (y0 + r) * a.pitch;
         if (VEC) {
             T *dst = reinterpret_cast<T *>(drow) + lane * 8;
@@ -730,8 +747,8 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     // the last two (the row end; the second-to-last slice's extra chunk
     // reaches up to 15 bytes into the last slice).
     if (s == 0 || s + 2 >= a.nsx) {
-        for (int r = lane; r < nr; r += 32) {
-            unsigned char *drow = tile + r * RB;
+        for (int r = r0 + lane; r < r1; r += 32) {
+            unsigned char *drow = tile + (r - r0) * RB;
             const char *row = a.img + (y0 + r) * a.pitch;
             if (VEC) {
                 const int64_t xl = (a.cols - s * kSliceCols) & ~(int64_t)7;   // partial lane's x
@@ -763,6 +780,7 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     }
     cp_async_wait_all();
     __syncwarp();
+    };
 
     // Reduce: column sums (8 per lane), row sums (lane keeps rows lane + 32 j).
     uint64_t cs[8], cq[8];
@@ -771,15 +789,22 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
         uint32_t c32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         QA cqa[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         // Rows go in groups of 32 (group j unrolled, so rs_s[j] and rs_q[j]
-        // have compile-time indices and stay in registers).
+        // have compile-time indices and stay in registers), staged parts from
+        // the bottom one up (sums do not depend on the order).
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) {
+        for (int jj = 0; jj < RPL; ++jj) {
+            const int j = (RPL / GPP - 1 - jj / GPP) * GPP + jj % GPP;
+            const int base = j / GPP * SR;             // first row of j's staged part
+            if (jj % GPP == 0) {
+                if (jj) __syncwarp();                  // the previous part is read
+                if (base < nr) stage(base);
+            }
             rs_s[j] = 0;
             rs_q[j] = 0;
             const int rend = min(nr, 32 * (j + 1));
             for (int r = 32 * j; r < rend; ++r) {
                 uint32_t px[8];
-                px_of(tile + r * RB, r, px);
+                px_of(tile + (r - base) * RB, r, px);
                 uint32_t rs = 0;
                 QA rq = 0;
 #pragma unroll
@@ -851,12 +876,17 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     for (int j = 0; j < RPL; ++j) {
         // Group j of 32 rows (unrolled: lr_s[j] has a compile-time index).
         const uint64_t ls = lr_s[j], lq = lr_q[j];
+        const int base = j / GPP * SR;                 // first row of j's staged part
+        if (j && j % GPP == 0 && base < nr) {          // parts below the top one
+            __syncwarp();                              // the previous part is read
+            stage(base);
+        }
         const int rend = min(nr, 32 * (j + 1));
         for (int r = 32 * j; r < rend; r += 2) {
             uint32_t pa[8], pb[8];
-            px_of(tile + r * RB, r, pa);
-            // Row r+1 < TH exists in the buffer (stale when r+1 == nr, unused).
-            px_of(tile + (r + 1) * RB, r + 1, pb);
+            px_of(tile + (r - base) * RB, r, pa);
+            // Row r+1 of the part exists in the buffer (stale when r+1 == nr, unused).
+            px_of(tile + (r + 1 - base) * RB, r + 1, pb);
             // r is even, so rows r and r+1 lie in the same group of 32.
             const uint64_t ha_s = H_s + __shfl_sync(kFull, ls, r & 31);
             const uint64_t hb_s = ha_s + __shfl_sync(kFull, ls, (r + 1) & 31);
@@ -912,7 +942,7 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
 template <typename T, int TH, bool WQ = true>
 constexpr int onepass_warp_bytes()
 {
-    return (ring_bytes<WQ>() + TH * tile_row_bytes<T>() + 1023) / 1024 * 1024;
+    return (ring_bytes<WQ>() + staged_rows<T, TH>() * tile_row_bytes<T>() + 1023) / 1024 * 1024;
 }
 
 // The warp's ring and tile inside the block's dynamic shared memory; warps
