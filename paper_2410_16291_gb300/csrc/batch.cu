@@ -66,11 +66,13 @@ struct BatchArgs {
 // Warps per build block: 9 (as many as the SM's shared memory holds) or 8;
 // a configuration choice the autotuner may make.
 constexpr int kBatchWarpsMax = 9;
+// uint16 tiles: 64 rows, staged in two 32-row parts (see onepass_tile).
+constexpr int kBatchU16Rows = 64;
 // Shared memory per warp: the larger of the uint8 (64-row) and uint16 tile
 // routines, so warps working on different dtypes never overlap.
 constexpr int kBatchWarpBytes =
-    onepass_warp_bytes<uint8_t, 64>() > onepass_warp_bytes<uint16_t, 32>()
-        ? onepass_warp_bytes<uint8_t, 64>() : onepass_warp_bytes<uint16_t, 32>();
+    onepass_warp_bytes<uint8_t, 64>() > onepass_warp_bytes<uint16_t, kBatchU16Rows>()
+        ? onepass_warp_bytes<uint8_t, 64>() : onepass_warp_bytes<uint16_t, kBatchU16Rows>();
 
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *tm)
 {
@@ -214,8 +216,8 @@ __global__ void __launch_bounds__(W * 32, 1) k_batch(const __grid_constant__ Bat
             ok = im.vec ? batch_tile<uint8_t, true, TH8>(im, tl, a.err, w)
                         : batch_tile<uint8_t, false, TH8>(im, tl, a.err, w);
         else
-            ok = im.vec ? batch_tile<uint16_t, true, 32>(im, tl, a.err, w)
-                        : batch_tile<uint16_t, false, 32>(im, tl, a.err, w);
+            ok = im.vec ? batch_tile<uint16_t, true, kBatchU16Rows>(im, tl, a.err, w)
+                        : batch_tile<uint16_t, false, kBatchU16Rows>(im, tl, a.err, w);
         if (!ok) break;
     }
     cp_async_wait_all();
@@ -296,7 +298,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
             set_error("batch item %d: a table entry could exceed 2^64-1", i);
             return SWA_EOVERFLOW;
         }
-        const int th = it.dtype == SWA_U8 ? th8 : 32;
+        const int th = it.dtype == SWA_U8 ? th8 : kBatchU16Rows;
         tiles += ((it.rows + th - 1) / th) * ((it.cols + kSliceCols - 1) / kSliceCols);
         for (int32_t k = 0; k < it.n_windows; ++k) {
             const swa_window &w = it.windows[k];
@@ -352,7 +354,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     for (int32_t pos = 0; pos < n; ++pos) {
         const int32_t i = order[pos];
         const swa_batch_item &it = items[i];
-        const int th = it.dtype == SWA_U8 ? th8 : 32;
+        const int th = it.dtype == SWA_U8 ? th8 : kBatchU16Rows;
         BImg &m = himg[pos];
         memset(&m, 0, sizeof(m));
         m.rows = it.rows;
