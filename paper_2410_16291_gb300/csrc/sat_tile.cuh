@@ -192,6 +192,13 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+__device__ __forceinline__ uint64_t l2_evict_last_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 __device__ __forceinline__ uint64_t l2_evict_first_policy()
 {
     uint64_t pol;
@@ -398,6 +405,15 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *g)
                  : "memory");
 }
 
+// cp_async16 with an L2 cache policy (evict-last for lines read again soon,
+// evict-first for their last read).
+__device__ __forceinline__ void cp_async16_hint(void *smem, const void *g, uint64_t pol)
+{
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                     smem_addr(smem)), "l"(g), "l"(pol)
+                 : "memory");
+}
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *g)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(g)
@@ -432,7 +448,8 @@ struct WarpRes {
     unsigned char *ring;              // [kRing][S, Q][2 KB]
     int slot;
     int sw[4];
-    uint64_t pol;
+    uint64_t pol;                     // L2 evict-first (table rows, last reads)
+    uint64_t pol_keep;                // L2 evict-last (pixels staged twice)
 };
 
 // Adds the column records (S, and Q with WQ) of the n tiles first, first-1,
@@ -713,7 +730,9 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     // the row are zero-filled here; pieces that straddle an end of the row
     // are left for the pass below, which loads their bytes one row per lane.
     constexpr int NCH = kSliceCols * (int)sizeof(T) / 16 + 1;
-    auto stage = [&](int r0) {
+    // hint: 0 none; 1 the part is staged again later (keep its lines in L2);
+    // 2 the part's second staging (their last read).
+    auto stage = [&](int r0, int hint) {
     const int r1 = min(nr, r0 + SR);
     for (int r = r0; r < r1; ++r) {
         unsigned char *drow = tile + (r - r0) * RB;
@@ -723,6 +742,7 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
             const T *src = reinterpret_cast<const T *>(row) + x;
             if (x + 8 <= a.cols) {
                 if (sizeof(T) == 1) cp_async8(dst, src);
+                else if (hint) cp_async16_hint(dst, src, hint == 1 ? w.pol_keep : w.pol);
                 else cp_async16(dst, src);
             } else if (x >= a.cols) {
 #pragma unroll
@@ -736,7 +756,10 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
                 if (k >= NCH) break;
                 const int64_t off = xb - m + 16 * k;          // chunk's offset in the row
                 uint4 *d = reinterpret_cast<uint4 *>(drow + 16 * k);
-                if (off >= 0 && off + 16 <= rowbytes) cp_async16(d, row + off);
+                if (off >= 0 && off + 16 <= rowbytes) {
+                    if (hint) cp_async16_hint(d, row + off, hint == 1 ? w.pol_keep : w.pol);
+                    else cp_async16(d, row + off);
+                }
                 else if (off >= rowbytes) *d = make_uint4(0u, 0u, 0u, 0u);
             }
         }
@@ -797,7 +820,7 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
             const int base = j / GPP * SR;             // first row of j's staged part
             if (jj % GPP == 0) {
                 if (jj) __syncwarp();                  // the previous part is read
-                if (base < nr) stage(base);
+                if (base < nr) stage(base, base ? 1 : 0);
             }
             rs_s[j] = 0;
             rs_q[j] = 0;
@@ -879,7 +902,7 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
         const int base = j / GPP * SR;                 // first row of j's staged part
         if (j && j % GPP == 0 && base < nr) {          // parts below the top one
             __syncwarp();                              // the previous part is read
-            stage(base);
+            stage(base, 2);
         }
         const int rend = min(nr, 32 * (j + 1));
         for (int r = 32 * j; r < rend; r += 2) {
@@ -962,6 +985,7 @@ __device__ __forceinline__ WarpRes warp_res(unsigned char *smem_raw,
 #pragma unroll
     for (int j = 0; j < 4; ++j) w.sw[j] = swz_off(lane, j);
     w.pol = l2_evict_first_policy();
+    w.pol_keep = l2_evict_last_policy();
     return w;
 }
 
