@@ -7,8 +7,9 @@
 //     row by row), each processed by the single-pass tile routine with
 //     decoupled look-back inside its image.
 //  2. k_batch_windows: one launch evaluates every query of every image; a
-//     block covers 1024 consecutive windows of one output row of one query
-//     and finds its query by binary search over the queries' block offsets.
+//     block covers 1024 consecutive windows of one output row of one query,
+//     taken from a schedule that walks each image's queries down its tables
+//     together (output rows merged by their first table row).
 //
 // The windows run in a launch of their own because the build's tiles need
 // 25 KB of shared memory per warp (9 warps per SM), while the window
@@ -54,9 +55,16 @@ struct BQuery {
     uint32_t item_base, nitems;       // first block, blocks
 };
 
+// One block of the query launch: its query and its block within the query
+// (output row blk / nbx, column block blk % nbx).
+struct BItem {
+    uint32_t q, blk;
+};
+
 struct BatchArgs {
     const BImg *imgs;
     const BQuery *qs;
+    const BItem *sched;               // the query launch's blocks, in launch order
     int32_t nimg, nq;
     uint32_t total_tiles, total_items;
     uint32_t *ticket, *err;
@@ -122,16 +130,19 @@ __device__ __forceinline__ bool batch_tile(const BImg &im, uint32_t t, uint32_t 
 constexpr int kBWinPerThread = 4;
 constexpr int kBWinPerBlock = 256 * kBWinPerThread;
 
-// Queries of all images: block -> query by binary search, then 1024
-// consecutive windows of one output row (thread t: t, t+256, t+512, t+768).
-__global__ void __launch_bounds__(256) k_batch_windows(const BQuery *__restrict__ qs, int32_t nq,
+// Queries of all images: block -> (query, block within the query) from the
+// launch's schedule, then 1024 consecutive windows of one output row (thread
+// t: t, t+256, t+512, t+768).  Results leave with streaming stores
+// (st.global.cs): nothing reads them back in this launch, so they should not
+// push the table rows that the image's other queries read next out of L2.
+__global__ void __launch_bounds__(256) k_batch_windows(const BQuery *__restrict__ qs,
+                                                       const BItem *__restrict__ sched,
                                                        const BImg *__restrict__ imgs)
 {
-    const uint32_t bid = blockIdx.x;
-    const int qi = find_base(nq, bid, [&](int i) { return qs[i].item_base; });
-    const BQuery &q = qs[qi];
+    const BItem item = sched[blockIdx.x];
+    const BQuery &q = qs[item.q];
     const BImg &im = imgs[q.img];
-    const uint32_t blk = bid - q.item_base;
+    const uint32_t blk = item.blk;
     const uint32_t nbx = (uint32_t)q.nbx;
     const uint32_t i = blk / nbx;
     const int64_t jb = (int64_t)(blk - i * nbx) * kBWinPerBlock + threadIdx.x;
@@ -153,25 +164,26 @@ __global__ void __launch_bounds__(256) k_batch_windows(const BQuery *__restrict_
         if (left) sw -= __ldg(Sb + x0 - 1);
         if (top && left) sw += __ldg(St + x0 - 1);
         const int64_t oi = orow + j;
-        if (o & SWA_OUT_SUM) q.w.sum[oi] = sw;
+        if (o & SWA_OUT_SUM) __stcs(reinterpret_cast<unsigned long long *>(q.w.sum) + oi, sw);
         if (o & SWA_OUT_MEAN)
-            q.w.mean[oi] = q.int_rn ? rn::mean_rn(sw, q.div)
-                                    : __ddiv_rn(__ull2double_rn(sw), q.n_d);
+            __stcs(q.w.mean + oi, q.int_rn ? rn::mean_rn(sw, q.div)
+                                           : __ddiv_rn(__ull2double_rn(sw), q.n_d));
         if (o & SWA_OUT_STD) {
             uint64_t qw = __ldg(Qb + x1);
             if (top) qw -= __ldg(Qt + x1);
             if (left) qw -= __ldg(Qb + x0 - 1);
             if (top && left) qw += __ldg(Qt + x0 - 1);
+            double sd;
             if (q.int_rn) {
-                q.w.std[oi] = q.d64 ? rn::std_rn64(q.n, sw, qw, q.div)
-                                    : rn::std_rn(q.n, sw, qw, q.div);
+                sd = q.d64 ? rn::std_rn64(q.n, sw, qw, q.div) : rn::std_rn(q.n, sw, qw, q.div);
             } else {
                 const unsigned __int128 D =
                     (unsigned __int128)q.n * qw - (unsigned __int128)sw * sw;
                 const double dd =
                     rn::fp_to_double(rn::round_u128((uint64_t)(D >> 64), (uint64_t)D));
-                q.w.std[oi] = __ddiv_rn(__dsqrt_rn(dd), q.n_d);
+                sd = __ddiv_rn(__dsqrt_rn(dd), q.n_d);
             }
+            __stcs(q.w.std + oi, sd);
         }
     }
 }
@@ -328,6 +340,8 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     off = align256(off + (int64_t)sizeof(BImg) * n);
     const int64_t off_qs = off;
     off = align256(off + (int64_t)sizeof(BQuery) * (nq ? nq : 1));
+    const int64_t off_sched = off;
+    off = align256(off + (int64_t)sizeof(BItem) * (items_w ? items_w : 1));
     const int64_t zero_off = off;                      // ticket, err, flags
     const int64_t off_ticket = off, off_err = off + 4;
     const int64_t off_flags = off + 256;
@@ -423,8 +437,10 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     // Queries in image order.
     uint32_t item_base = 0;
     int64_t qk = 0;
+    std::vector<int64_t> q_first(n + 1, 0);           // image pos: queries [q_first[pos], q_first[pos+1])
     for (int32_t pos = 0; pos < n; ++pos) {
         const swa_batch_item &it = items[order[pos]];
+        q_first[pos] = qk;
         for (int32_t k = 0; k < it.n_windows; ++k) {
             const swa_window &w = it.windows[k];
             BQuery &q = hq[qk++];
@@ -452,11 +468,41 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
             item_base += q.nitems;
         }
     }
+    q_first[n] = qk;
+    // Launch order of the query blocks: image by image; within an image, its
+    // queries' output rows merged by the table row their windows start at
+    // (y0 = i * sy), so all of the image's queries move down its tables
+    // together and read each table row while the others' reads keep it in
+    // L2, instead of each query sweeping the whole tables on its own.
+    std::vector<BItem> hs(item_base ? item_base : 1);
+    {
+        struct RowKey {
+            int64_t y0;
+            uint32_t q, i;
+        };
+        std::vector<RowKey> rows;
+        size_t o = 0;
+        for (int32_t pos = 0; pos < n; ++pos) {
+            rows.clear();
+            for (int64_t k = q_first[pos]; k < q_first[pos + 1]; ++k)
+                for (int64_t i = 0; i < hq[k].w.R; ++i)
+                    rows.push_back(RowKey{i * hq[k].w.sy, (uint32_t)k, (uint32_t)i});
+            std::stable_sort(rows.begin(), rows.end(),
+                             [](const RowKey &x, const RowKey &y) { return x.y0 < y.y0; });
+            for (const RowKey &r : rows) {
+                const uint32_t nbx = (uint32_t)hq[r.q].nbx;
+                for (uint32_t bx = 0; bx < nbx; ++bx) hs[o++] = BItem{r.q, r.i * nbx + bx};
+            }
+        }
+    }
     cudaError_t e;
     if ((e = cudaMemcpyAsync(base + off_imgs, himg.data(), sizeof(BImg) * n,
                              cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (nq && (e = cudaMemcpyAsync(base + off_qs, hq.data(), sizeof(BQuery) * nq,
                                     cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
+        (item_base && (e = cudaMemcpyAsync(base + off_sched, hs.data(),
+                                           sizeof(BItem) * item_base, cudaMemcpyHostToDevice,
+                                           s)) != cudaSuccess) ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess) {
         set_error("uploading batch descriptors: %s", cudaGetErrorString(e));
         dev_free(b->mem, b->mem_bytes, s);
@@ -470,6 +516,7 @@ swa_status swa_batch_create(const swa_batch_item *items, int32_t n, const swa_ba
     BatchArgs &a = b->args;
     a.imgs = reinterpret_cast<const BImg *>(base + off_imgs);
     a.qs = reinterpret_cast<const BQuery *>(base + off_qs);
+    a.sched = reinterpret_cast<const BItem *>(base + off_sched);
     a.nimg = n;
     a.nq = (int32_t)nq;
     a.total_tiles = tile_base;
@@ -509,7 +556,7 @@ swa_status swa_batch_run(swa_batch *b, swa_stream stream)
     }
     if (b->total_items) {
         LaunchScope ls("batch_windows", s);
-        k_batch_windows<<<b->total_items, 256, 0, s>>>(b->args.qs, b->args.nq, b->args.imgs);
+        k_batch_windows<<<b->total_items, 256, 0, s>>>(b->args.qs, b->args.sched, b->args.imgs);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -123,6 +123,32 @@ __device__ __forceinline__ uint64_t ld_corner(const uint64_t *p)
 // on a 64-bit D.
 constexpr int kRnFp64 = 0, kRnInt128 = 1, kRnInt64 = 2;
 
+// Sum, mean and std of the window at output index o from its moments.  The
+// results leave with streaming stores (st.global.cs): nothing reads them
+// back in the launch, so they should not push out of L2 the table rows and
+// lattice entries that later windows' corners read.
+template <bool DO_SUM, bool DO_MEAN, bool DO_STD, int RN>
+__device__ __forceinline__ void store_stats(const WinQ &q, int64_t o, uint64_t sw, uint64_t qw)
+{
+    if (DO_SUM) __stcs(reinterpret_cast<unsigned long long *>(q.w.sum) + o, sw);
+    if (DO_MEAN)
+        __stcs(q.w.mean + o,
+               RN != kRnFp64 ? rn::mean_rn(sw, q.div) : __ddiv_rn(__ull2double_rn(sw), q.n_d));
+    if (DO_STD) {
+        double sd;
+        if (RN == kRnInt64) {
+            sd = rn::std_rn64(q.n, sw, qw, q.div);
+        } else if (RN == kRnInt128) {
+            sd = rn::std_rn(q.n, sw, qw, q.div);
+        } else {
+            const unsigned __int128 D = (unsigned __int128)q.n * qw - (unsigned __int128)sw * sw;
+            const double d = u128_to_double_rn((uint64_t)(D >> 64), (uint64_t)D);
+            sd = __ddiv_rn(__dsqrt_rn(d), q.n_d);
+        }
+        __stcs(q.w.std + o, sd);
+    }
+}
+
 // The WPT windows (i, jb), (i, jb + 256), ... of one query: all corner loads
 // first (independent, so they are in flight together), then the arithmetic.
 // With TL, the top-left corner's S and Q entries are given (tl_s, tl_q:
@@ -165,23 +191,7 @@ __device__ __forceinline__ void window_row(const WinArgs &a, const WinQ &q, int6
     for (int m = 0; m < WPT; ++m) {
         const int64_t j = jb + 256 * m;
         if (j >= q.w.C) break;
-        const int64_t o = orow + j;
-        if (DO_SUM) q.w.sum[o] = sw[m];
-        if (DO_MEAN)
-            q.w.mean[o] =
-                RN != kRnFp64 ? rn::mean_rn(sw[m], q.div) : __ddiv_rn(__ull2double_rn(sw[m]), q.n_d);
-        if (DO_STD) {
-            if (RN == kRnInt64) {
-                q.w.std[o] = rn::std_rn64(q.n, sw[m], qw[m], q.div);
-            } else if (RN == kRnInt128) {
-                q.w.std[o] = rn::std_rn(q.n, sw[m], qw[m], q.div);
-            } else {
-                const unsigned __int128 D =
-                    (unsigned __int128)q.n * qw[m] - (unsigned __int128)sw[m] * sw[m];
-                const double d = u128_to_double_rn((uint64_t)(D >> 64), (uint64_t)D);
-                q.w.std[o] = __ddiv_rn(__dsqrt_rn(d), q.n_d);
-            }
-        }
+        store_stats<DO_SUM, DO_MEAN, DO_STD, RN>(q, orow + j, sw[m], qw[m]);
     }
 }
 
@@ -248,21 +258,7 @@ __device__ __forceinline__ void window_shared(const WinArgs &a, const WinQ &q, i
     const uint64_t tl_s = sh_tl[t], tl_q = DO_STD ? sh_tl[256 + t] : 0;
     const uint64_t sw = br_s - tr_s - bl_s + tl_s;
     const uint64_t qw = DO_STD ? br_q - tr_q - bl_q + tl_q : 0;
-    const int64_t o = i * q.w.out_ld + jb;
-    if (DO_SUM) q.w.sum[o] = sw;
-    if (DO_MEAN)
-        q.w.mean[o] = RN != kRnFp64 ? rn::mean_rn(sw, q.div) : __ddiv_rn(__ull2double_rn(sw), q.n_d);
-    if (DO_STD) {
-        if (RN == kRnInt64) {
-            q.w.std[o] = rn::std_rn64(q.n, sw, qw, q.div);
-        } else if (RN == kRnInt128) {
-            q.w.std[o] = rn::std_rn(q.n, sw, qw, q.div);
-        } else {
-            const unsigned __int128 D = (unsigned __int128)q.n * qw - (unsigned __int128)sw * sw;
-            const double d = u128_to_double_rn((uint64_t)(D >> 64), (uint64_t)D);
-            q.w.std[o] = __ddiv_rn(__dsqrt_rn(d), q.n_d);
-        }
-    }
+    store_stats<DO_SUM, DO_MEAN, DO_STD, RN>(q, i * q.w.out_ld + jb, sw, qw);
 }
 
 // Dense column strides: every group holds one query; a block covers 1,024
