@@ -42,6 +42,12 @@ INSTR_PER_WINDOW = 400.6
 # exact shifts), from ncu on the 8,192 x 16,384 case with windows 256/1024 at
 # stride 16 (profiles/window_stats_lattice_8192x16384.md).
 INSTR_PER_WINDOW_LATTICE_POW2 = 296.0
+# The same for the batched engine's query kernel over the batched workload's
+# mix (uint8 and uint16 images, windows 16-512 at strides 1-8, a quarter of
+# them on the 128-bit path), from ncu on its first 8 images
+# (profiles/batch_8images.md): 1.4829e9 warp instructions x 31.79 active
+# threads / 112.6 M windows.
+INSTR_PER_WINDOW_BATCH = 418.5
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e datasheet bandwidth, for context beside the measured peak
 
@@ -689,6 +695,12 @@ def batch_measure(args, local_rank, steps, plain_steps, n_images=0, dist=False):
     build_algo = sum(im.pixels * ((2 if im.dtype == "u16" else 1) + 16) for im in imgs)
     build = batch_kernels.get("batch_build", {}).get("ms_per_pass")
     query = batch_kernels.get("batch_windows", {}).get("ms_per_pass")
+    # The query kernel is bound by instruction issue: thread instructions it
+    # needs per second against 152 SMs x 4 schedulers x 32 lanes x the
+    # sampled SM clock.
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    issue_peak = sms * 4 * 32 * ((clk or {}).get("sm_mhz") or 2070.0) * 1e6
+    q_rate = n_out * INSTR_PER_WINDOW_BATCH / (query / 1e3) if query else None
     rec = {"ms": ms, "gpx_s": px / (ms / 1e3) / 1e9,
            "window_outputs_per_s": n_out / (ms / 1e3),
            "images": len(imgs), "pixels": px, "window_outputs": n_out, "batch_config": cfg,
@@ -697,6 +709,9 @@ def batch_measure(args, local_rank, steps, plain_steps, n_images=0, dist=False):
            "build_ms": build, "query_ms": query,
            "build_hbm_frac": (build_algo / (build / 1e3) / 1e9 / hbm) if build else None,
            "build_algorithmic_bytes": build_algo, "peak_kind": hbm_kind,
+           "query_issue_frac": q_rate / issue_peak if q_rate else None,
+           "query_instructions_per_window": INSTR_PER_WINDOW_BATCH,
+           "issue_peak_tinst_s": issue_peak / 1e12,
            "kernels": batch_kernels,
            "plain_path": {"ms_per_pass": plain_ms, "gpx_s": px / (plain_ms / 1e3) / 1e9,
                           "launches_per_pass": plain_launches, "kernels": plain_kernels,
@@ -725,7 +740,25 @@ def run_batch(args, rank, world, local_rank):
         return
     ms = rec["ms"]
     hbm, hbm_kind = peaks()
-    algo = rec["build_algorithmic_bytes"] + 24 * rec["window_outputs"]
+    # The roofline of the pass's dominant kernel: the query kernel (bound by
+    # instruction issue) or the build (bound by HBM), each on its own
+    # event-timed duration; the other one's fraction stays beside it.
+    build_roof = {"bound": "hbm", "kernel": "k_batch",
+                  "achieved": rec["build_algorithmic_bytes"] / (rec["build_ms"] / 1e3) / 1e9,
+                  "peak": hbm, "unit": "GB/s", "frac": rec["build_hbm_frac"],
+                  "peak_kind": hbm_kind,
+                  "algorithmic_bytes_per_launch": rec["build_algorithmic_bytes"],
+                  "traffic": traffic_record("k_batch")}
+    if rec["query_ms"] and rec["query_ms"] > rec["build_ms"]:
+        peak_t = rec["issue_peak_tinst_s"]
+        roof = {"bound": "alu", "kernel": "k_batch_windows",
+                "achieved": rec["query_issue_frac"] * peak_t, "peak": peak_t,
+                "unit": "Tinst/s", "frac": rec["query_issue_frac"],
+                "peak_kind": "152 SMs x 4 schedulers x 32 lanes x sampled SM clock",
+                "instructions_per_window": rec["query_instructions_per_window"],
+                "traffic": None}
+    else:
+        roof = build_roof
     line = {"metric": METRIC, "value": world * rec["pixels"] / (ms / 1e3) / 1e9,
             "unit": "Gpx/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -740,10 +773,7 @@ def run_batch(args, rank, world, local_rank):
             "window_outputs_per_s": world * rec["window_outputs"] / (ms / 1e3),
             "kernels": rec["kernels"], "plain_path": rec["plain_path"],
             "speedup_vs_plain": rec["speedup_vs_plain"],
-            "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": algo / (ms / 1e3) / 1e9,
-                         "peak": hbm, "unit": "GB/s", "frac": algo / (ms / 1e3) / 1e9 / hbm,
-                         "peak_kind": hbm_kind, "algorithmic_bytes_per_launch": algo,
-                         "traffic": traffic_record("k_batch")},
+            "roofline": roof, "build_roofline": build_roof,
             "build_ms": rec["build_ms"], "query_ms": rec["query_ms"],
             "build_hbm_frac": rec["build_hbm_frac"], "plan_bytes": rec["plan_bytes"],
             "gpu_launches": args.steps * rec["gpu_launches_per_pass"],
