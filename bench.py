@@ -35,8 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "SAT build Gpx/s + window outputs/s, % HBM peak; served p50/p99 vs plain path"
 # Thread instructions per window (sum, mean, std; 4 windows per thread) of
 # the window kernel, from ncu on the 12,288^2 stride-1 case
-# (profiles/window_stats_dense_12288x12288.md).
-INSTR_PER_WINDOW = 400.6
+# (profiles/window_stats_dense_12288x12288.md): 1.8474e9 warp instructions x
+# 31.99 active threads / 148.57 M windows.
+INSTR_PER_WINDOW = 397.8
 # The same for windows served from the corner lattice of the default
 # workload (window areas 256^2 and 1024^2, powers of two: the divisions are
 # exact shifts), from ncu on the 8,192 x 16,384 case with windows 256/1024 at

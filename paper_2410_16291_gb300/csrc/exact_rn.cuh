@@ -17,11 +17,12 @@
 //     giving a 54- or 55-bit quotient and an exact remainder for the sticky
 //     bit;
 //   - square root: an FP32 reciprocal-square-root seed, two Newton
-//     corrections computed from exact integer residuals N - R^2 (the second
-//     one rounded to the nearest integer, which leaves R within 0.51 of
-//     sqrt(N)), then one exact step to the nearest integer: R is nearest iff
-//     -R < N - R^2 <= R (sqrt(N) is an integer or irrational, never a
-//     half-integer).
+//     corrections computed from exact integer residuals N - R^2 (32 of their
+//     bits at a fixed position, converted with 32-bit conversions; the
+//     second correction rounded to the nearest integer, which leaves R
+//     within 0.51 of sqrt(N)), then one exact step to the nearest integer: R
+//     is nearest iff -R < N - R^2 <= R (sqrt(N) is an integer or irrational,
+//     never a half-integer).
 // The functions are __host__ __device__ so a CPU test can compare them with
 // the host's IEEE arithmetic bit for bit.
 #pragma once
@@ -93,58 +94,48 @@ SWA_HD float approx_rsqrt(float x)
 #endif
 }
 
-// float estimate of a signed 64-bit integer.  On the device the conversion
-// instruction is used (it issues to the FP64 pipe, which this code otherwise
-// leaves idle, while the integer work keeps the ALU pipe busy); the host
-// version truncates to 24 bits with integer operations.
-SWA_HD float i64_to_float_trunc(int64_t v)
+// 32-bit conversions between integers and float, IEEE-rounded as named, on
+// the device by the conversion instructions and on the host by C's
+// conversions (which round the same way).  The square root below uses only
+// these: GB300 runs 64-bit integer conversions at its FP64 rate, about two
+// per SM per clock.
+SWA_HD float i32_to_float_rn(int32_t v)
 {
 #if defined(__CUDA_ARCH__)
-    return __ll2float_rz(v);
-#endif
-    if (v == 0) return 0.0f;
-    const uint32_t sign = v < 0 ? 0x80000000u : 0u;
-    const uint64_t mag = v < 0 ? (uint64_t)0 - (uint64_t)v : (uint64_t)v;
-    const int lz = clz64(mag);
-    const uint64_t m = mag << lz;                       // top bit at 63
-    return bits_to_float(sign | ((uint32_t)(127 + 63 - lz) << 23) |
-                         ((uint32_t)(m >> 40) & 0x7fffffu));
-}
-
-SWA_HD uint32_t float_bits(float f)
-{
-#if defined(__CUDA_ARCH__)
-    return __float_as_uint(f);
+    return __int2float_rn(v);
 #else
-    uint32_t b;
-    __builtin_memcpy(&b, &f, 4);
-    return b;
+    return (float)v;
 #endif
 }
 
-// Signed 64-bit integer nearest to a float with |x| < 2^62 (ties to even).
-SWA_HD int64_t float_to_i64_rn(float x)
+// |x| < 2^31, truncated toward zero.
+SWA_HD int32_t float_to_i32_rz(float x)
 {
 #if defined(__CUDA_ARCH__)
-    return __float2ll_rn(x);
+    return __float2int_rz(x);
 #else
-    return (int64_t)llrintf(x);
+    return (int32_t)x;
 #endif
 }
 
-// Signed 64-bit integer from a float with |x| < 2^62, truncating toward zero
-// (the conversion instruction on the device, integer operations on the host).
-SWA_HD int64_t float_to_i64_trunc(float x)
+// |x| < 2^31, to the nearest integer (ties to even).
+SWA_HD int32_t float_to_i32_rn(float x)
 {
 #if defined(__CUDA_ARCH__)
-    return __float2ll_rz(x);
+    return __float2int_rn(x);
+#else
+    return (int32_t)nearbyintf(x);
 #endif
-    const uint32_t b = float_bits(x);
-    const int e = (int)((b >> 23) & 0xffu) - 127;
-    if (e < 0) return 0;
-    const uint64_t m = (b & 0x7fffffu) | 0x800000u;
-    const uint64_t mag = e >= 23 ? m << (e - 23) : m >> (23 - e);
-    return (b >> 31) ? -(int64_t)mag : (int64_t)mag;
+}
+
+// 0 <= x < 2^32, truncated toward zero.
+SWA_HD uint32_t float_to_u32_rz(float x)
+{
+#if defined(__CUDA_ARCH__)
+    return __float2uint_rz(x);
+#else
+    return (uint32_t)x;
+#endif
 }
 
 // A value sig * 2^exp with sig < 2^53 (sig == 0 means zero).
@@ -295,18 +286,22 @@ SWA_HD void residual(uint64_t Nhi, uint64_t Nlo, uint64_t R, int64_t *rhi, uint6
 
 // RN(sqrt(sig * 2^exp)) for 1 <= sig < 2^53.
 //
-// Error budget: the seed R0 = fx * rsqrt(fx) * 2^26 has relative error below
-// 2^-21 (24-bit truncation of Mx, rsqrtf within 2 ulp, two float roundings),
-// so |R0 - sqrt(N)| < 2^32.  A correction R += (N - R^2) / (2R), with the
-// quotient formed in FP32 from the exact residual (relative error below
-// 2^-20 with the truncation of the residual to its top 64 bits), leaves
-// |R1 - sqrt(N)| < 2^12 (2^11 from the quotient's error, 2^11 from Newton's
-// quadratic term, 1 from truncating the step).  The second correction's
-// quotient error is then below 2^12 * 2^-20 = 2^-8 and its quadratic term
-// below 2^-28; rounding the step to the nearest integer adds at most 1/2, so
-// |R2 - sqrt(N)| < 0.51.  Hence N - R2^2 lies within (2 sqrt(N) + 1) * 0.51
-// < 2^54 of zero: its low 64 bits, read as a signed integer, are its value,
-// and the nearest integer to sqrt(N) is R2 - 1, R2 or R2 + 1.
+// Error budget.  N = Mx * 2^52 with 2^52 <= Mx < 2^54, so 2^52 <= sqrt(N) <
+// 2^53.  The seed R0 = fx * rsqrt(fx) * 2^26 has relative error below 2^-21
+// (24-bit truncation of Mx, rsqrtf within 2 ulp, one float rounding), so
+// e0 = R0 - sqrt(N) has |e0| < 2^32.  A correction R += c * (N - R^2) with
+// c = y * 2^-27 ~ 1/(2 sqrt(N)) leaves R - sqrt(N) = -e * (eps + e/(2 sqrt(N))
+// + eps * e/(2 sqrt(N))), where eps < 2^-21 is the relative error of the
+// float quotient (y, the residual's conversion and one product).
+//   First: the residual |N - R0^2| < 2^86.01 enters as its bits 56..87
+//   (an int32, floor), and the step is truncated to a multiple of 4; these
+//   add below 8 + 4, so |e1| < 2^11 + 2^11 + 12.
+//   Second: |N - R1^2| < 2^66.01 enters as its bits 36..67 (an int32;
+//   floor, below 2^-17 in the step), and the step is rounded to the
+//   nearest integer, so |e2| < 1/2 + 2^-9 + 2^-17 + 2^-28 < 0.51.
+// Hence N - R2^2 lies within (2 sqrt(N) + 1) * 0.51 < 2^54 of zero: its low
+// 64 bits, read as a signed integer, are its value, and the nearest integer
+// to sqrt(N) is R2 - 1, R2 or R2 + 1.
 SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
 {
     const int L = 64 - clz64(sig);
@@ -319,17 +314,20 @@ SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
     const float fx = bits_to_float(((uint32_t)(LM - 1 + 127) << 23) |
                                    ((uint32_t)(Mx >> (LM - 24)) & 0x7fffffu));
     const float y = approx_rsqrt(fx);
-    uint64_t R = (uint64_t)float_to_i64_trunc(fx * y * 67108864.0f);   // 2^26
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        int64_t rh;
-        uint64_t rl;
-        residual(Nhi, Nlo, R, &rh, &rl);
-        // (rh:rl) >> 32 fits int64 (|N - R^2| < 2^95)
-        const int64_t top = (int64_t)(((uint64_t)rh << 32) | (rl >> 32));
-        const float dlt = i64_to_float_trunc(top) * y * 32.0f;   // * 2^32 / 2^27
-        R = (uint64_t)((int64_t)R + (it ? float_to_i64_rn(dlt) : float_to_i64_trunc(dlt)));
-    }
+    // fx * y * 16 lies in [2^30, 2^31) up to the seed's error: a float whose
+    // integer part is itself, so R0 = that integer * 2^22 exactly.
+    uint64_t R = (uint64_t)float_to_u32_rz(fx * y * 16.0f) << 22;
+    int64_t rh;
+    uint64_t rl;
+    residual(Nhi, Nlo, R, &rh, &rl);
+    const int32_t t1 = (int32_t)(uint32_t)(((uint64_t)rh << 8) | (rl >> 56));
+    // step / 4 = t1 * 2^56 * y * 2^-27 / 4 = t1 * y * 2^27, |.| < 2^30.01
+    R = (uint64_t)((int64_t)R +
+                   4 * (int64_t)float_to_i32_rz(i32_to_float_rn(t1) * y * 134217728.0f));
+    residual(Nhi, Nlo, R, &rh, &rl);
+    const int32_t t2 = (int32_t)(uint32_t)(((uint64_t)rh << 28) | (rl >> 36));
+    // step = t2 * 2^36 * y * 2^-27 = t2 * y * 2^9, |.| < 2^12.01
+    R = (uint64_t)((int64_t)R + float_to_i32_rn(i32_to_float_rn(t2) * y * 512.0f));
     const int64_t rem = (int64_t)(Nlo - R * R);    // N - R^2, |.| < 2^54
     if (rem > (int64_t)R) ++R;
     else if (rem <= -(int64_t)R) --R;
