@@ -41,14 +41,15 @@ INSTR_PER_WINDOW = 397.8
 # The same for windows served from the corner lattice of the default
 # workload (window areas 256^2 and 1024^2, powers of two: the divisions are
 # exact shifts), from ncu on the 8,192 x 16,384 case with windows 256/1024 at
-# stride 16 (profiles/window_stats_lattice_8192x16384.md).
-INSTR_PER_WINDOW_LATTICE_POW2 = 296.0
+# stride 16 (profiles/window_stats_lattice_8192x16384.md): 8.5546e6 warp
+# instructions x 31.37 active threads / 932,962 windows.
+INSTR_PER_WINDOW_LATTICE_POW2 = 287.6
 # The same for the batched engine's query kernel over the batched workload's
 # mix (uint8 and uint16 images, windows 16-512 at strides 1-8, a quarter of
 # them on the 128-bit path), from ncu on its first 8 images
-# (profiles/batch_8images.md): 1.4829e9 warp instructions x 31.79 active
+# (profiles/batch_8images.md): 1.4740e9 warp instructions x 31.79 active
 # threads / 112.6 M windows.
-INSTR_PER_WINDOW_BATCH = 418.5
+INSTR_PER_WINDOW_BATCH = 416.0
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e datasheet bandwidth, for context beside the measured peak
 
