@@ -304,15 +304,16 @@ SWA_HD void residual(uint64_t Nhi, uint64_t Nlo, uint64_t R, int64_t *rhi, uint6
 // to sqrt(N) is R2 - 1, R2 or R2 + 1.
 SWA_HD Fp sqrt_rn(uint64_t sig, int exp)
 {
-    const int L = 64 - clz64(sig);
-    uint64_t Mx = sig << (53 - L);                 // [2^52, 2^53)
-    int E = exp - (53 - L);
-    if (E & 1) { Mx <<= 1; E -= 1; }              // [2^52, 2^54), E even
+    // Mx = sig shifted to 53 bits, and one bit further when that leaves an
+    // odd exponent: Mx in [2^52, 2^54) with 53 + odd bits, E even.
+    const int t = 53 - (64 - clz64(sig));
+    const int odd = (exp - t) & 1;
+    const uint64_t Mx = sig << (t + odd);
+    const int E = exp - t - odd;
     const uint64_t Nhi = Mx >> 12, Nlo = Mx << 52; // N = Mx * 2^52
     // FP32 seed: y ~ 1/sqrt(Mx); R0 ~ sqrt(N) = sqrt(Mx) * 2^26.
-    const int LM = 64 - clz64(Mx);                 // 53 or 54
-    const float fx = bits_to_float(((uint32_t)(LM - 1 + 127) << 23) |
-                                   ((uint32_t)(Mx >> (LM - 24)) & 0x7fffffu));
+    const float fx = bits_to_float(((uint32_t)(52 + odd + 127) << 23) |
+                                   ((uint32_t)(Mx >> (29 + odd)) & 0x7fffffu));
     const float y = approx_rsqrt(fx);
     // fx * y * 16 lies in [2^30, 2^31) up to the seed's error: a float whose
     // integer part is itself, so R0 = that integer * 2^22 exactly.
