@@ -33,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SAT build Gpx/s + window outputs/s, % HBM peak; served p50/p99 vs plain path"
-# Thread instructions per window (sum, mean, std; 4 windows per thread) of
+# Thread instructions per window (sum, mean, std; 2 windows per thread) of
 # the window kernel, from ncu on the 12,288^2 stride-1 case
 # (profiles/window_stats_dense_12288x12288.md): 1.8474e9 warp instructions x
 # 31.99 active threads / 148.57 M windows.

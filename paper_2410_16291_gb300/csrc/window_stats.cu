@@ -79,16 +79,19 @@ struct WinArgs {
     WinGroup g[kQPerLaunch];
 };
 
-// Windows per thread: 4 (256 apart) where the arithmetic dominates, i.e.
+// Windows per thread: 2 (256 apart) where the arithmetic dominates, i.e.
 // dense column strides whose corner loads mostly hit the same sectors; 1
 // where the gather dominates (column stride >= kSparseStride: neighbouring
 // threads' corners lie 24 bytes or more apart, so most corner loads touch
 // their own sector, and more resident warps hide more latency).  Measured
-// on 20,000^2 with windows 50 and 100: stride 2 runs faster dense (3.09 vs
-// 3.24 ms), stride 3 sparse (1.46 vs 1.65 ms), stride 6 sparse (0.56 vs
-// 0.70 ms).
+// on 20,000^2 with windows 50 and 100 (with 4 dense windows per thread):
+// stride 2 runs faster dense (3.09 vs 3.24 ms), stride 3 sparse (1.46 vs
+// 1.65 ms), stride 6 sparse (0.56 vs 0.70 ms).  Two dense windows per thread
+// instead of four fit the 64-bit-D path in 32 registers (8 blocks per SM
+// instead of 6): workload 1's windows 15.21 -> 14.61 ms.
 constexpr int kSparseStride = 3;
-inline int wins_per_thread(int64_t sx) { return sx >= kSparseStride ? 1 : 4; }
+constexpr int kDenseWpt = 2;
+inline int wins_per_thread(int64_t sx) { return sx >= kSparseStride ? 1 : kDenseWpt; }
 
 // Column panel width (blocks of 256 windows) of sparse-stride groups.  With
 // about 1,200 resident blocks a 4-block panel keeps ~300 grid rows in
@@ -261,19 +264,31 @@ __device__ __forceinline__ void window_shared(const WinArgs &a, const WinQ &q, i
     store_stats<DO_SUM, DO_MEAN, DO_STD, RN>(q, i * q.w.out_ld + jb, sw, qw);
 }
 
-// Dense column strides: every group holds one query; a block covers 1,024
-// consecutive windows of one output row (thread t: windows t, t + 256,
-// t + 512, t + 768, so every load and store instruction stays coalesced).
+// Blocks per SM the dense kernel asks the compiler to fit (at most 65,536 /
+// (256 x blocks) registers a thread): 8 on the 64-bit-D path, which needs no
+// more than 32 registers for two windows a thread (ptxas: 27-32, no spills);
+// 6 where the 128-bit path or the FP64 sequence need more, and for std
+// alone, which would spill at 32.
+template <bool DO_SUM, bool DO_MEAN, int RN>
+constexpr int dense_min_blocks()
+{
+    return RN == kRnInt64 && (DO_SUM || DO_MEAN) ? 8 : 6;
+}
+
+// Dense column strides: every group holds one query; a block covers 512
+// consecutive windows of one output row (thread t: windows t and t + 256,
+// so every load and store instruction stays coalesced).
 template <bool DO_SUM, bool DO_MEAN, bool DO_STD, int RN>
-__global__ void __launch_bounds__(256) k_windows_dense(const __grid_constant__ WinArgs a)
+__global__ void __launch_bounds__(256, (dense_min_blocks<DO_SUM, DO_MEAN, RN>()))
+    k_windows_dense(const __grid_constant__ WinArgs a)
 {
     const uint32_t bid = blockIdx.x;
     const WinGroup &G = group_of(a, bid);
     const uint32_t blk = bid - (uint32_t)G.first_block;
     const uint32_t nbx = (uint32_t)G.nbx;
     const uint32_t i = blk / nbx;
-    const int64_t jb = (int64_t)(blk - i * nbx) * (256 * 4) + threadIdx.x;
-    window_row<DO_SUM, DO_MEAN, DO_STD, RN, 4>(a, a.q[G.q0], i, jb);
+    const int64_t jb = (int64_t)(blk - i * nbx) * (256 * kDenseWpt) + threadIdx.x;
+    window_row<DO_SUM, DO_MEAN, DO_STD, RN, kDenseWpt>(a, a.q[G.q0], i, jb);
 }
 
 // Sparse column strides: a block covers 256 consecutive positions of one
