@@ -35,21 +35,21 @@ sys.path.insert(0, ROOT)
 METRIC = "SAT build Gpx/s + window outputs/s, % HBM peak; served p50/p99 vs plain path"
 # Thread instructions per window (sum, mean, std; 2 windows per thread) of
 # the window kernel, from ncu on the 12,288^2 stride-1 case
-# (profiles/window_stats_dense_12288x12288.md): 1.8474e9 warp instructions x
+# (profiles/window_stats_dense_12288x12288.md): 1.8691e9 warp instructions x
 # 31.99 active threads / 148.57 M windows.
-INSTR_PER_WINDOW = 397.8
+INSTR_PER_WINDOW = 402.4
 # The same for windows served from the corner lattice of the default
 # workload (window areas 256^2 and 1024^2, powers of two: the divisions are
 # exact shifts), from ncu on the 8,192 x 16,384 case with windows 256/1024 at
-# stride 16 (profiles/window_stats_lattice_8192x16384.md): 8.5546e6 warp
-# instructions x 31.37 active threads / 932,962 windows.
-INSTR_PER_WINDOW_LATTICE_POW2 = 287.6
+# stride 16 (profiles/window_stats_lattice_8192x16384.md): 8.8121e6 warp
+# instructions x 31.43 active threads / 932,962 windows.
+INSTR_PER_WINDOW_LATTICE_POW2 = 296.9
 # The same for the batched engine's query kernel over the batched workload's
 # mix (uint8 and uint16 images, windows 16-512 at strides 1-8, a quarter of
 # them on the 128-bit path), from ncu on its first 8 images
-# (profiles/batch_8images.md): 1.4740e9 warp instructions x 31.79 active
+# (profiles/batch_8images.md): 1.4485e9 warp instructions x 31.79 active
 # threads / 112.6 M windows.
-INSTR_PER_WINDOW_BATCH = 416.0
+INSTR_PER_WINDOW_BATCH = 408.8
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e datasheet bandwidth, for context beside the measured peak
 
