@@ -414,13 +414,16 @@ template <typename T> constexpr int onepass_rows() { return 64; }
 
 // Warps per block of the single-pass build: as many independent warps as
 // the shared memory of one SM holds (227 KB per block, 1 KB for alignment),
-// at most 16.  One block runs per SM.
+// at most 14 (14 x 32 threads x 144 registers fill the SM's 65,536; the
+// tile routine needs up to 140).  One block runs per SM.
 constexpr int kSmemPerBlock = 227 * 1024;
+constexpr int kOnePassMaxWarps = 14;
 template <typename T, bool WQ> constexpr int onepass_warps()
 {
-    return (kSmemPerBlock - 1024) / onepass_warp_bytes<T, onepass_rows<T>(), WQ>() < 16
+    return (kSmemPerBlock - 1024) / onepass_warp_bytes<T, onepass_rows<T>(), WQ>() <
+                   kOnePassMaxWarps
                ? (kSmemPerBlock - 1024) / onepass_warp_bytes<T, onepass_rows<T>(), WQ>()
-               : 16;
+               : kOnePassMaxWarps;
 }
 
 template <typename T, bool WQ, bool VEC, bool THR = false, bool LAT = false>

@@ -136,9 +136,12 @@ template <typename T>
 constexpr int tile_row_bytes() { return kSliceCols * (int)sizeof(T) + 16; }
 
 // Rows of a TH-row tile staged at a time: all of them while they hold at most
-// 16 KB of pixels (256 columns of uint8 up to 64 rows), else 32-row parts.
-template <typename T, int TH>
-constexpr int staged_rows() { return TH * (int)sizeof(T) <= 64 ? TH : 32; }
+// 16 KB of pixels (256 columns of uint8 up to 64 rows) and the build writes
+// S and Q, else 32-row parts.  A build of S alone (count tables, sum-only
+// tables) writes half the bytes per tile for about the same work per tile,
+// so it trades the second staging of a part for more warps per SM.
+template <typename T, int TH, bool WQ = true>
+constexpr int staged_rows() { return (TH * (int)sizeof(T) <= 64 && WQ) ? TH : 32; }
 
 // The lane's 8 pixels of one staged row.  VEC rows hold the slice's pixels
 // from byte 0; other rows hold the 16-byte-aligned chunks covering the
@@ -402,6 +405,13 @@ __device__ __forceinline__ void publish(uint32_t *f1, uint32_t v1, uint32_t *f2 
 __device__ __forceinline__ void cp_async8(void *smem, const void *g)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(g)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async8_hint(void *smem, const void *g, uint64_t pol)
+{
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(
+                     smem_addr(smem)), "l"(g), "l"(pol)
                  : "memory");
 }
 
@@ -696,7 +706,7 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
     // reduced bottom part first, so the top part is still staged when the
     // scan begins; the other parts are staged again for their scan (from L2,
     // which has just read them).
-    constexpr int SR = staged_rows<T, TH>();
+    constexpr int SR = staged_rows<T, TH, WQ>();
     constexpr int GPP = SR / 32;                       // 32-row groups per staged part
     static_assert(SR % 32 == 0 && TH % SR == 0, "staged parts are whole 32-row groups");
     unsigned char *tile = w.tile;
@@ -741,8 +751,10 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
             T *dst = reinterpret_cast<T *>(drow) + lane * 8;
             const T *src = reinterpret_cast<const T *>(row) + x;
             if (x + 8 <= a.cols) {
-                if (sizeof(T) == 1) cp_async8(dst, src);
-                else if (hint) cp_async16_hint(dst, src, hint == 1 ? w.pol_keep : w.pol);
+                if (sizeof(T) == 1) {
+                    if (hint) cp_async8_hint(dst, src, hint == 1 ? w.pol_keep : w.pol);
+                    else cp_async8(dst, src);
+                } else if (hint) cp_async16_hint(dst, src, hint == 1 ? w.pol_keep : w.pol);
                 else cp_async16(dst, src);
             } else if (x >= a.cols) {
 #pragma unroll
@@ -965,7 +977,8 @@ __device__ __forceinline__ bool onepass_tile(const TileCtx &a, uint32_t t, uint3
 template <typename T, int TH, bool WQ = true>
 constexpr int onepass_warp_bytes()
 {
-    return (ring_bytes<WQ>() + staged_rows<T, TH>() * tile_row_bytes<T>() + 1023) / 1024 * 1024;
+    return (ring_bytes<WQ>() + staged_rows<T, TH, WQ>() * tile_row_bytes<T>() + 1023) / 1024 *
+           1024;
 }
 
 // The warp's ring and tile inside the block's dynamic shared memory; warps

@@ -291,3 +291,23 @@ def test_workload0_cell_mask():
     np.testing.assert_array_equal(u64(o["sum"]), want)
     assert o["sum"].shape == (993, 993)
     sat.free()
+
+
+OUTPUT_SETS = [("sum",), ("mean",), ("std",), ("sum", "mean"), ("sum", "std"), ("mean", "std"),
+               ("sum", "mean", "std")]
+
+
+@pytest.mark.parametrize("outputs", OUTPUT_SETS, ids=["+".join(o) for o in OUTPUT_SETS])
+@pytest.mark.parametrize("stride", [1, 2, 4])
+def test_every_output_selection(outputs, stride):
+    """Each selection of outputs runs its own kernel instantiation (dense
+    column strides 1-2, sparse from 3; the 64-bit-D and 128-bit-D rounding
+    paths): all of them must equal the oracle.  On a uint16 image a 31 x 17
+    window takes the 64-bit-D path (n * 65535 < 2^32), a 300 x 300 one the
+    128-bit path."""
+    img = rand_img(700, 1100, np.uint16)
+    sat = swa.build_sat(to_device(img), with_sq=True)
+    S_ref, Q_ref = oracle.sat(img)
+    check_windows(sat, S_ref, Q_ref, [(31, 17, stride, stride), (300, 300, stride, stride)],
+                  outputs=outputs)
+    sat.free()
