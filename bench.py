@@ -224,27 +224,32 @@ def distinct_corner_bytes_all(rows, cols, windows, tables):
 
 def traffic_record(kernel, case=None):
     """ncu DRAM bytes per launch for `kernel` on the workload `case` (e.g.
-    "70000x85000 u8 S+Q"), if the committed capture is of the current source
-    and was scaled to that case; else None."""
+    "70000x85000 u8 S+Q lattice 16"), if a committed capture of that case is
+    of the current source; else None.  A kernel's entry is one record or a
+    list of them, one per captured case."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
     import hashlib
     with open(p) as f:
         d = json.load(f)
-    e = d.get(kernel)
-    if not e or e.get("full_case") != case:
-        return None
-    names = e["source"] if isinstance(e["source"], list) else [e["source"]]
-    h = hashlib.sha256()
-    for name in names:                       # the kernel's sources, in order
-        src = os.path.join(ROOT, "paper_2410_16291_gb300", "csrc", name)
-        if not os.path.exists(src):
+    recs = d.get(kernel)
+    if isinstance(recs, dict):
+        recs = [recs]
+    for e in recs or []:
+        if e.get("full_case") != case:
+            continue
+        names = e["source"] if isinstance(e["source"], list) else [e["source"]]
+        h = hashlib.sha256()
+        for name in names:                   # the kernel's sources, in order
+            src = os.path.join(ROOT, "paper_2410_16291_gb300", "csrc", name)
+            if not os.path.exists(src):
+                return None
+            h.update(open(src, "rb").read())
+        if h.hexdigest()[:16] != e["source_sha"]:
             return None
-        h.update(open(src, "rb").read())
-    if h.hexdigest()[:16] != e["source_sha"]:
-        return None
-    return e["bytes_per_launch_full"]
+        return e["bytes_per_launch_full"]
+    return None
 
 
 # --------------------------------------------------------------- CPU legs --
