@@ -123,22 +123,27 @@ HOOKS = {"default": 0, "corner": swa.SWA_HOOK_CORNER_MODE, "row": swa.SWA_HOOK_R
          "corner+row": swa.SWA_HOOK_CORNER_MODE | swa.SWA_HOOK_ROW_ORDER}
 
 
+@pytest.mark.parametrize("with_sq", [True, False], ids=["S+Q", "S"])
 @pytest.mark.parametrize("hook", list(HOOKS))
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 @pytest.mark.parametrize("shape,pad,offset", [((129, 32768), 0, 0), ((200, 32775), 3, 1),
                                               ((67, 40000), 0, 0), ((5, 33000), 8, 3),
                                               ((1000, 1031), 0, 2), ((300, 5000), 5, 0)])
-def test_tables_lookback_modes(hook, dtype, shape, pad, offset):
+def test_tables_lookback_modes(hook, dtype, shape, pad, offset, with_sq):
+    """Tables of S and Q, and of S alone (whose uint8 tiles are staged in two
+    parts), in all four look-back / ticket-order combinations, on wide,
+    short, pitched and unaligned images."""
     img = rand_img(*shape, dtype)
     L = swa.lib()
     assert L.swa_set_test_hooks(HOOKS[hook]) == 0
     try:
-        sat = swa.build_sat(to_device(img, pad_cols=pad, offset_px=offset), with_sq=True)
+        sat = swa.build_sat(to_device(img, pad_cols=pad, offset_px=offset), with_sq=with_sq)
         sat.sync()
     finally:
         L.swa_set_test_hooks(0)
-    S_ref, Q_ref = check_tables(sat, img)
-    check_windows(sat, S_ref, Q_ref, [(min(33, shape[0]), 1000, 4, 7), (shape[0], shape[1], 1, 1)])
+    S_ref, Q_ref = check_tables(sat, img, with_sq=with_sq)
+    check_windows(sat, S_ref, Q_ref, [(min(33, shape[0]), 1000, 4, 7), (shape[0], shape[1], 1, 1)],
+                  outputs=("sum", "mean", "std") if with_sq else ("sum", "mean"))
     sat.free()
 
 
