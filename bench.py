@@ -47,9 +47,9 @@ INSTR_PER_WINDOW_LATTICE_POW2 = 296.9
 # The same for the batched engine's query kernel over the batched workload's
 # mix (uint8 and uint16 images, windows 16-512 at strides 1-8, a quarter of
 # them on the 128-bit path), from ncu on its first 8 images
-# (profiles/batch_8images.md): 1.4485e9 warp instructions x 31.79 active
+# (profiles/batch_8images.md): 1.5378e9 warp instructions x 31.79 active
 # threads / 112.6 M windows.
-INSTR_PER_WINDOW_BATCH = 408.8
+INSTR_PER_WINDOW_BATCH = 434.0
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e datasheet bandwidth, for context beside the measured peak
 
