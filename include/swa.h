@@ -347,7 +347,14 @@ typedef struct {
     int32_t ticket_order;       /* each image's tiles: 0 along anti-diagonals; 1 row by row */
     int32_t lookback;           /* 0: edge records (the default); 1: corner records */
     int32_t warps;              /* warps per build block: 9 or 8 (0: 9) */
-    int32_t reserved[3];        /* must be 0 */
+    int32_t interleave;         /* images whose tiles share the build's work queue at
+                                 * a time, their tickets merged by each image's
+                                 * progress (every image keeps its own tile order):
+                                 * 1 image after image; n > 1 groups of up to n
+                                 * images that run the same tile routine (pixel
+                                 * type, aligned rows or not), the images ordered
+                                 * by that kind first (0: 8) */
+    int32_t reserved[2];        /* must be 0 */
 } swa_batch_config;
 
 typedef struct swa_batch swa_batch;

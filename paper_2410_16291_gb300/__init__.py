@@ -48,7 +48,8 @@ class swa_batch_item(ctypes.Structure):
 class swa_batch_config(ctypes.Structure):
     """Mirror of ``swa_batch_config`` in swa.h."""
     _fields_ = [("u8_tile_rows", _I32), ("order", _I32), ("ticket_order", _I32),
-                ("lookback", _I32), ("warps", _I32), ("reserved", _I32 * 3)]
+                ("lookback", _I32), ("warps", _I32), ("interleave", _I32),
+                ("reserved", _I32 * 2)]
 
 
 class swa_kernel_time(ctypes.Structure):
@@ -404,7 +405,8 @@ class Batch:
     """
 
     def __init__(self, images, windows, outputs=("sum", "mean", "std"), u8_tile_rows=64,
-                 order=0, stream=None, out=None, ticket_order=0, lookback=0, warps=0):
+                 order=0, stream=None, out=None, ticket_order=0, lookback=0, warps=0,
+                 interleave=0):
         import torch
         mask = (SWA_OUT_SUM if "sum" in outputs else 0) | (
             SWA_OUT_MEAN if "mean" in outputs else 0) | (SWA_OUT_STD if "std" in outputs else 0)
@@ -440,7 +442,7 @@ class Batch:
             items[k] = swa_batch_item(img.data_ptr(), rows, cols,
                                       img.stride(0) * img.element_size(), _dtype_code(img),
                                       len(wl), arr)
-        cfg = swa_batch_config(u8_tile_rows, order, ticket_order, lookback, warps)
+        cfg = swa_batch_config(u8_tile_rows, order, ticket_order, lookback, warps, interleave)
         h = _VP()
         self.stream = stream
         check(lib().swa_batch_create(items, len(self.images), ctypes.byref(cfg),

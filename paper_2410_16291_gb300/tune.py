@@ -11,9 +11,11 @@ results:
   or row by row);
 - the look-back mode (edge records, or corner records from the tile above
   and to the left);
-- the warps per build block (9, as many as shared memory holds, or 8).
+- the warps per build block (9, as many as shared memory holds, or 8);
+- how many images of the same kind share the build's work queue at a time
+  (8, their tickets merged by progress, or 1, image after image).
 
-``tune`` times every combination (32 candidates) on a deterministic sample
+``tune`` times every combination (64 candidates) on a deterministic sample
 of the batch's images with CUDA events and keeps the fastest.  Results are
 cached in a JSON file keyed by the device and a coarse description of the
 batch, so a later batch of the same kind skips the search.  The cache file
@@ -28,11 +30,11 @@ import math
 import os
 
 AXES = (("u8_tile_rows", (64, 32)), ("order", (0, 1)), ("ticket_order", (0, 1)),
-        ("lookback", (0, 1)), ("warps", (9, 8)))
+        ("lookback", (0, 1)), ("warps", (9, 8)), ("interleave", (8, 1)))
 # Every combination, the library's defaults first.
 CANDIDATES = tuple(dict(zip([k for k, _ in AXES], v))
                    for v in itertools.product(*[vals for _, vals in AXES]))
-KEY_VERSION = 2
+KEY_VERSION = 3
 
 
 def cache_path() -> str:

@@ -122,7 +122,7 @@ def test_batch_config_checked_on_the_host(L):
     items = (swa.swa_batch_item * 1)(item)
     h = ctypes.c_void_p()
     for bad in [dict(u8_tile_rows=48), dict(order=2), dict(ticket_order=-1), dict(lookback=2),
-                dict(warps=7), dict(reserved=(ctypes.c_int32 * 3)(0, 1, 0))]:
+                dict(warps=7), dict(interleave=-1), dict(reserved=(ctypes.c_int32 * 2)(0, 1))]:
         cfg = swa.swa_batch_config(**bad)
         assert L.swa_batch_create(items, 1, ctypes.byref(cfg), None, ctypes.byref(h)) == \
             swa.SWA_EINVAL, bad

@@ -54,11 +54,14 @@ def check_batch(batch, imgs, wins):
 
 
 @pytest.mark.parametrize("cfg", [
-    dict(u8_tile_rows=64, order=0), dict(u8_tile_rows=32, order=1),
+    dict(u8_tile_rows=64, order=0), dict(u8_tile_rows=32, order=1, interleave=1),
     dict(u8_tile_rows=64, order=0, ticket_order=1, lookback=1, warps=8),
     dict(u8_tile_rows=32, order=0, ticket_order=1, lookback=0, warps=9),
     dict(u8_tile_rows=64, order=1, ticket_order=0, lookback=1, warps=9),
-    dict(u8_tile_rows=32, order=1, ticket_order=0, lookback=0, warps=8)],
+    dict(u8_tile_rows=32, order=1, ticket_order=0, lookback=0, warps=8),
+    dict(u8_tile_rows=64, order=0, interleave=4),
+    dict(u8_tile_rows=64, order=1, ticket_order=1, lookback=1, interleave=1000),
+    dict(u8_tile_rows=32, order=0, ticket_order=0, lookback=0, warps=8, interleave=3)],
     ids=lambda c: "-".join("%s%d" % (k[:2], v) for k, v in c.items()))
 def test_batch_bitexact_and_repeatable(cfg):
     """Every configuration the autotuner may pick gives the same, exact

@@ -6,10 +6,10 @@ from paper_2410_16291_gb300 import tune
 
 
 def test_candidates_cover_every_combination_defaults_first():
-    assert len(tune.CANDIDATES) == 32
+    assert len(tune.CANDIDATES) == 64
     assert tune.CANDIDATES[0] == {"u8_tile_rows": 64, "order": 0, "ticket_order": 0,
-                                  "lookback": 0, "warps": 9}
-    assert len({tuple(sorted(c.items())) for c in tune.CANDIDATES}) == 32
+                                  "lookback": 0, "warps": 9, "interleave": 8}
+    assert len({tuple(sorted(c.items())) for c in tune.CANDIDATES}) == 64
 
 
 def test_choose_picks_fastest_and_breaks_ties_in_order():
@@ -42,14 +42,15 @@ def test_tune_uses_timer_and_cache(tmp_path, monkeypatch):
     wins = [[(16, 16, 1, 1)]] * 40
     calls = []
 
-    want = {"u8_tile_rows": 32, "order": 1, "ticket_order": 0, "lookback": 1, "warps": 8}
+    want = {"u8_tile_rows": 32, "order": 1, "ticket_order": 0, "lookback": 1, "warps": 8,
+            "interleave": 1}
 
     def timer(cfg, ii, ww):
         calls.append((dict(cfg), len(ii)))
         return 1.0 if cfg == want else 2.0
     best = tune.tune(imgs, wins, sample=8, timer=timer)
     assert best == want
-    assert len(calls) == 32 and all(n == 8 for _, n in calls)
+    assert len(calls) == 64 and all(n == 8 for _, n in calls)
     data = json.load(open(tmp_path / "t.json"))
     assert list(data.values())[0]["config"] == best
     calls.clear()
