@@ -556,11 +556,22 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
         et = max_over_ranks(sum(times) / len(times), device="cuda")
+        # The host link alone, for comparison: plain uploads of the same
+        # pinned image (its bytes are most of what a call moves).
+        link = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            dev.copy_(host, non_blocking=True)
+            torch.cuda.synchronize()
+            link.append(time.perf_counter() - t0)
+        med = statistics.median(times)
         e2e = {"value": job_throughput(px, et, world) / 1e9, "unit": "Gpx/s",
                "h2d_bytes_per_step": px, "d2h_bytes_per_step": 24 * n_out,
                "ms_per_step": et * 1e3, "steps": args.e2e_steps,
-               "ms_median": 1e3 * statistics.median(times), "ms_min": 1e3 * min(times),
+               "ms_median": 1e3 * med, "ms_min": 1e3 * min(times),
                "ms_max": 1e3 * max(times),
+               "calls_over_1_5x_median": sum(1 for t in times if t > 1.5 * med),
+               "link_upload_ms_median": 1e3 * statistics.median(link),
                "api": "swa_analyze (pinned host image in, pinned host results out; "
                       "host images of 256 MiB or more stream in bands)"}
 
