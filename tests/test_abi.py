@@ -26,7 +26,7 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(swa_[a-z0-9_]+)\s*\(", text)))
 
 
-def test_header_declares_the_survey_calls():
+def test_header_declares_the_boundary_calls():
     names = declared_functions()
     for n in ("swa_build_sat", "swa_window_stats", "swa_free", "swa_window_shape",
               "swa_sat_data", "swa_sync", "swa_status_str"):
