@@ -1,4 +1,6 @@
 """The server's resident-table cache and memory budget (CPU, fake tables)."""
+import pytest
+
 from paper_2410_16291_gb300.serve import TableCache, _Entry
 
 
@@ -14,7 +16,7 @@ class FakeSat:
 
 def test_reserve_evicts_least_recently_used_unreferenced():
     FakeSat.freed = []
-    c = TableCache(100)
+    c = TableCache(100, policy="lru")
     for k in "abc":
         assert c.reserve(30)
         c.insert(k, _Entry(FakeSat(k), 30))
@@ -25,6 +27,29 @@ def test_reserve_evicts_least_recently_used_unreferenced():
     assert FakeSat.freed == ["c"] and c.used == 100 and c.evictions == 1
     assert c.reserve(1)              # full: evicts a (unreferenced), not b
     assert FakeSat.freed == ["c", "a"] and c.used == 71 and list(c.entries) == ["b"]
+
+
+def test_lfu_evicts_the_least_asked_for_first_then_the_least_recent():
+    FakeSat.freed = []
+    c = TableCache(100)                  # policy "lfu"
+    for k in "abc":
+        assert c.reserve(30)
+        c.insert(k, _Entry(FakeSat(k), 30))
+    for k, n in (("a", 1), ("b", 3), ("c", 2)):
+        for _ in range(n):
+            c.count(k)
+    c.get("b")
+    c.get("c")                           # LRU order now a, b, c
+    c.get("a")                           # ... b, c, a: LRU would evict b first
+    assert c.reserve(40)                 # a was asked for least often: a goes
+    assert FakeSat.freed == ["a"] and c.used == 100
+    c.count("b")                         # b: 4, c: 2
+    assert c.reserve(30)                 # c next (fewer requests than b)
+    assert FakeSat.freed == ["a", "c"] and list(c.entries) == ["b"]
+    c.insert("a", _Entry(FakeSat("a2"), 30))     # counts outlive an eviction
+    assert c.freq["a"] == 1 and c.freq["c"] == 2
+    with pytest.raises(ValueError):
+        TableCache(10, policy="fifo")
 
 
 def test_reserve_fails_when_everything_is_referenced():
