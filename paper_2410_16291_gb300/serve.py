@@ -179,7 +179,8 @@ def output_bytes(rows, cols, windows):
 
 
 class Server:
-    """Continuous-batching server with a resident-table LRU cache.
+    """Continuous-batching server with a resident-table cache (least often
+    requested tables evicted first).
 
     budget_bytes: device memory the server may hold at once.
     streams: number of CUDA streams requests are spread over, or a list of
