@@ -163,3 +163,36 @@ def test_latency_summary_skips_failed_requests():
     rs[3].error = "table build failed"
     out = latency_summary(rs)
     assert out["requests"] == 3 and out["failed"] == 1 and out["max_ms"] == 30.0
+
+
+def _replay(policy, budget):
+    """The served workload's 200-request trace in order through the cache
+    (each table freed before the next request): misses and table bytes
+    built."""
+    import paper_2410_16291_gb300 as swa
+    import synth
+    from paper_2410_16291_gb300 import build, serve
+    build.build()                            # table sizes come from the library (host only)
+    pool, trace = synth.serve_requests(200, synth.DEFAULT_SEED + 4)
+    c = TableCache(budget, policy=policy)
+    misses = built = 0
+    for _, idx, _ in trace:
+        im = pool[idx]
+        if c.get(idx) is None:
+            code = swa.SWA_U8 if im.dtype == "u8" else swa.SWA_U16
+            tab = serve.table_bytes(im.rows, im.cols, code)[0]
+            assert c.reserve(tab)
+            c.insert(idx, _Entry(FakeSat(idx), tab))
+            misses += 1
+            built += tab
+        c.count(idx)
+    return misses, built
+
+
+def test_frequency_aware_eviction_rebuilds_less_on_the_served_trace():
+    """The served workload's images have far more table bytes than the
+    budget; keeping the tables asked for most often rebuilds fewer of them
+    than keeping the most recent ones."""
+    for budget in (90 * 10**9, 100 * 10**9):
+        lfu, lru = _replay("lfu", budget), _replay("lru", budget)
+        assert lfu[0] < lru[0] and lfu[1] < lru[1], (budget, lfu, lru)
